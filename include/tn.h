@@ -1,0 +1,230 @@
+/*
+ * tn.h -- C ABI of libtn: exact inference on discrete graphical models by
+ * contracting the model's factor tensors along a binary contraction tree on
+ * one GB300 GPU (sm_103a).
+ *
+ * Method (arXiv 2405.14060, "Probabilistic Inference in the Era of Tensor
+ * Networks and Differential Programming"):
+ *   - a model is the tensor network (Lambda, T, {}) of its factors
+ *     (Sec. "Tensor networks for probabilistic modeling", Def. "Tensor Network");
+ *   - PR   p(e) = con(Lambda \ E, T_e, {})                          (Eq. pr)
+ *   - MAR  p(Q_i | e) from the gradients of unity tensors 1_{Q_i} added to the
+ *          network, one forward and one reverse pass                 (Sec. MAR,
+ *          Thm. "Tensor network differentiation", Eq. einback)
+ *   - MPE  tcon of the log-tensors in the max-plus semiring and the
+ *          configuration by back-propagating Boolean masks            (Sec. MPE,
+ *          Eq. log-map, Eq. tropical-back)
+ *   - MMAP sum-contract groups of tensors that hold every summed
+ *          variable, then MPE over the query variables                (Sec. MMAP)
+ *   - sampling: backward sampling through the cached contraction tree
+ *          (Sec. "Generative modeling", Eq. sample, Eq. condition-prob)
+ *
+ * Conventions
+ *   - Variables are 0..nvars-1 with domain sizes card[v] >= 1.
+ *   - Factor tables are row-major with the LAST scope variable fastest
+ *     (UAI convention), non-negative and finite.
+ *   - Evidence vectors are int32 [nvars]: observed value, or -1 if free.
+ *   - Logarithms are natural.
+ *   - Output buffers are owned by the caller.  Functions without the _dev
+ *     suffix take HOST pointers and copy through the library's stream; the
+ *     _dev variants take DEVICE pointers and enqueue on opts->cuda_stream
+ *     (0 = the legacy default stream) and return once the work is enqueued
+ *     and complete (they synchronise the stream before returning, so the
+ *     outputs are valid on return).
+ *   - No exception crosses the ABI.  Every call returns a tn_status; on
+ *     failure tn_last_error() describes the cause (thread-local string, valid
+ *     until the next call on the same thread).
+ *   - A model is not thread-safe: calls on one tn_model must not overlap.
+ */
+#ifndef TN_H
+#define TN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tn_model tn_model;   /* opaque, owned by the library */
+
+typedef enum {
+    TN_OK = 0,
+    TN_E_ARG = 1,          /* invalid argument (also: p(e) = 0 for MAR/MAP/sample) */
+    TN_E_PARSE = 2,        /* malformed UAI text */
+    TN_E_ORDER = 3,        /* invalid contraction tree */
+    TN_E_OOM = 4,          /* device memory or the HBM budget exhausted */
+    TN_E_CUDA = 5,         /* a CUDA call failed */
+    TN_E_TIMEOUT = 6,      /* a bounded device-side wait gave up */
+    TN_E_UNSUPPORTED = 7   /* valid request outside what this build supports */
+} tn_status;
+
+typedef enum {
+    TN_FP64 = 0,   /* every tensor and every operation in double */
+    TN_FP32 = 1,   /* float tensors, FP32 CUDA-core arithmetic */
+    TN_TF32 = 2,   /* float tensors; dense GEMM nodes on tcgen05 kind::tf32 */
+    TN_BF16 = 3    /* float tensors; dense GEMM nodes on tcgen05 kind::f16 (bf16) */
+} tn_prec;
+
+typedef struct {
+    tn_prec prec;               /* default TN_FP64 */
+    int64_t hbm_budget_bytes;   /* 0 = no limit beyond the device's memory */
+    int max_slices;             /* reserved (slicing is set by tn_set_order) */
+    int autotune;               /* 1 = let the tile autotuner time candidates */
+    void *cuda_stream;          /* cudaStream_t for the _dev variants; NULL = default */
+} tn_options;                   /* a NULL options pointer means all defaults */
+
+/* ------------------------------------------------------------ model */
+
+/* Parse a UAI-format MARKOV or BAYES file (Sec. Benchmarks uses the UAI
+ * competition format).  *out receives a new model (free with tn_free_model).
+ * Errors: TN_E_ARG (NULL arguments, unreadable file), TN_E_PARSE. */
+tn_status tn_load_model(const char *uai_path, tn_model **out);
+
+/* Build a model from arrays.  Factor f has scope
+ * scope_vars[scope_off[f] .. scope_off[f+1]) and its table starts at
+ * tables + (sum of the sizes of factors 0..f-1).  All arrays are host
+ * memory and are copied.  Errors: TN_E_ARG (bad domain size, scope variable
+ * out of range or repeated, negative or non-finite table entry). */
+tn_status tn_load_model_arrays(int nvars, const int *card, int nfactors,
+                               const int *scope_off, const int *scope_vars,
+                               const double *tables, tn_model **out);
+
+void tn_free_model(tn_model *m);
+
+/* ------------------------------------------------------- contraction order */
+
+/*
+ * Leaves of the contraction tree: ids 0..nfactors-1 are the factors, ids
+ * nfactors..nfactors+nvars-1 are the per-variable unity/evidence vectors
+ * (Sec. MAR step 1: one unity tensor per variable; an observed variable's
+ * vector is the indicator of its value, which equals slicing, Eq. pr).
+ * nleaves = nfactors + nvars.  Internal node i (0 <= i < nleaves-1) has id
+ * nleaves + i and children left[i], right[i], which must be ids of leaves or
+ * of earlier internal nodes; every id except the root is used exactly once
+ * (Sec. Tensor networks, binary contraction trees).  The last node is the root.
+ *
+ * nnodes = 0 with left = right = NULL selects the built-in greedy order
+ * (repeatedly contract the connected pair with the smallest size increase).
+ * slice_vars[0..nslice) are variables fixed per slice: the tree is contracted
+ * once per assignment of them and the results are combined (log-sum-exp for
+ * PR, weighted sums for MAR).  Errors: TN_E_ORDER (a malformed tree).
+ */
+tn_status tn_set_order(tn_model *m, int nnodes, const int *left, const int *right,
+                       int nslice, const int *slice_vars);
+
+/* Build a tree from a variable elimination order (a permutation of a subset
+ * of 0..nvars-1; variables not listed are eliminated last in id order): the
+ * tensors holding each variable are merged smallest-first and the variable
+ * is summed at the last merge.  Writes nleaves-1 entries to left/right. */
+tn_status tn_tree_from_elimination(const tn_model *m, int nelim, const int *order,
+                                   int *left, int *right);
+
+/* Search a contraction tree: method 0 = greedy (as tn_set_order's default),
+ * 1 = randomised min-fill / min-degree elimination with `restarts` restarts
+ * keeping the tree of least time complexity whose space complexity is
+ * minimal.  Writes nleaves-1 entries to left/right. */
+tn_status tn_optimize_order(const tn_model *m, int method, int restarts, uint64_t seed,
+                            int *left, int *right);
+
+/* Complexities of the current tree for `batch` evidence sets:
+ * out[0] = log2 of the total multiply-add count (time complexity, paper:
+ * product over the union of the labels of each pairwise contraction),
+ * out[1] = log2 of the largest intermediate's entry count (space complexity),
+ * out[2] = log2 of the total entries read and written (read-write complexity),
+ * out[3] = number of internal nodes, out[4] = forward FLOPs (2 per multiply-add),
+ * out[5] = forward algorithmic bytes at the given precision. */
+tn_status tn_tree_stats(const tn_model *m, int batch, tn_prec prec, double *out);
+
+/* ------------------------------------------------------------- tasks */
+
+/* PR: logz[b] = log p(e_b) for each of `batch` evidence sets evid[b][nvars]
+ * (Eq. pr).  log p(e) = -inf when the evidence is impossible. */
+tn_status tn_pr(tn_model *m, int batch, const int32_t *evid, const tn_options *opts,
+                double *logz);
+
+/* MAR: logz as tn_pr, and marg[b][sum card] = p(v = x | e_b) for every
+ * variable (an observed variable gets the indicator of its value).  One
+ * forward and one reverse (adjoint) pass over the tree (Sec. MAR).
+ * Errors: TN_E_ARG when some p(e_b) = 0. */
+tn_status tn_mar(tn_model *m, int batch, const int32_t *evid, const tn_options *opts,
+                 double *logz, double *marg);
+
+/* MPE: assign[nvars] maximises prod_f T_f given the evidence (observed
+ * variables keep their value); logp = log of that maximum (Eq. log-map).
+ * Ties go to the lowest flat index at each contraction.
+ * Errors: TN_E_ARG when p(e) = 0. */
+tn_status tn_map(tn_model *m, const int32_t *evid, const tn_options *opts,
+                 int32_t *assign, double *logp);
+
+/* MMAP: assign[nq] maximises sum_m p(q, m, e) over the query variables
+ * query[0..nq); logp = log of that maximum (Eq. mmap), by the two-phase
+ * method of Sec. MMAP (sum-contract groups, then max-plus over the query).
+ * The summed phase runs in FP64 when prec = TN_FP64, else in FP32 with
+ * power-of-two rescaling; the max-plus phase runs in FP64 / FP32 likewise.
+ * Errors: TN_E_ARG (query overlaps evidence, p(e) = 0), TN_E_OOM. */
+tn_status tn_mmap(tn_model *m, const int32_t *evid, int nq, const int32_t *query,
+                  const tn_options *opts, int32_t *assign, double *logp);
+
+/* Sampling: n exact samples of all variables from p(Lambda \ E | e) by
+ * backward sampling through the contraction tree (Sec. Generative modeling,
+ * Eq. condition-prob).  samples[n][nvars] (observed variables keep their
+ * value; domain sizes must be <= 127).  Random numbers: Philox4x32-10
+ * keyed by `seed`, one counter per (sample, node).
+ * Errors: TN_E_ARG when p(e) = 0. */
+tn_status tn_sample(tn_model *m, const int32_t *evid, uint64_t seed, int64_t n,
+                    const tn_options *opts, int8_t *samples);
+
+/* Device-pointer variants.  evid, logz, marg, factor_tables and grad live in
+ * device memory.  If factor_tables is non-NULL it replaces the model's
+ * tables for this call and later calls (same layout as tn_load_model_arrays,
+ * double); with tables_are_log != 0 its entries are the natural logarithms
+ * of the tables (exponentiated when the leaves are built).  The model's own
+ * tables come back on the next call without factor_tables.
+ * tn_mar_dev additionally writes, if grad is non-NULL, grad[b][sum of
+ * factor table sizes] = d log p(e_b) / d log T_f[x] = the factor marginal
+ * p(scope_f = x | e_b) (Thm. "Tensor network differentiation" applied to
+ * each factor). */
+tn_status tn_pr_dev(tn_model *m, int batch, const int32_t *evid,
+                    const double *factor_tables, int tables_are_log,
+                    const tn_options *opts, double *logz);
+tn_status tn_mar_dev(tn_model *m, int batch, const int32_t *evid,
+                     const double *factor_tables, int tables_are_log,
+                     const tn_options *opts, double *logz, double *marg, double *grad);
+
+/* Device-side duration of the last task's kernels in milliseconds
+ * (CUDA events around the launch on the task's stream). */
+double tn_last_device_ms(const tn_model *m);
+
+/* Number of kernel launches the last task issued (graph nodes counted). */
+int64_t tn_last_launch_count(const tn_model *m);
+
+const char *tn_last_error(void);
+
+/* ---------------------------------------------------- pairwise contraction */
+
+/*
+ * One pairwise contraction con({A, B} -> C) (Def. "Tensor Network",
+ * Eq. contraction-definition) on device buffers, with the labels of each
+ * operand given as small integers (storage order, last fastest) and
+ * sizes[label] the dimension of each label (labels 0..nlabels-1).
+ *   semiring 0: C = sum over the labels not in C of A * B
+ *   semiring 1: C = max over those labels of A + B (Eq. tropical), and if
+ *               argmax is non-NULL, argmax[c] = the flat index (first
+ *               eliminated label slowest, in the order: labels of A not in
+ *               C in A's order, then labels of B in neither A nor C in B's
+ *               order) of the first maximising assignment.
+ * dtype: 0 = double, 1 = float.  prec selects the kernel family for float
+ * (TN_FP32, TN_TF32, TN_BF16).  No rescaling is applied.  The call
+ * allocates its scratch memory from the library and synchronises `stream`.
+ */
+tn_status tn_contract_dev(int nlabels, const int *sizes,
+                          int na, const int *labels_a, const void *A,
+                          int nb, const int *labels_b, const void *B,
+                          int nc, const int *labels_c, void *C,
+                          int semiring, int dtype, tn_prec prec, int32_t *argmax,
+                          void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TN_H */

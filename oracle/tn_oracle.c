@@ -615,8 +615,17 @@ static void bte_add(bte_t *B, int i, int id) {
  * with no eliminated variable, and messages with empty scope, go to the
  * root list (parent -1).  Returns log of the product of all root items in
  * *lroot (sum mode) or their sum (max-sum mode). */
+static int bte_forward_k(int nvars, sliced_t *S, const int *order, int n, int op,
+                         bte_t *B, double *lroot, int keep);
+
 static int bte_forward(int nvars, sliced_t *S, const int *order, int n, int op,
                        bte_t *B, double *lroot) {
+    return bte_forward_k(nvars, S, order, n, op, B, lroot, 1);
+}
+
+/* keep = 0 frees every message once its receiving bucket has used it. */
+static int bte_forward_k(int nvars, sliced_t *S, const int *order, int n, int op,
+                         bte_t *B, double *lroot, int keep) {
     memset(B, 0, sizeof(*B));
     B->n = n;
     B->var = (int *)malloc(sizeof(int) * (size_t)(n ? n : 1));
@@ -663,6 +672,9 @@ static int bte_forward(int nvars, sliced_t *S, const int *order, int n, int op,
             int rc = multiply_eliminate(k, fl, B->var[i], op, &B->msg[i],
                                         op == OP_MAXSUM ? &B->am[i] : NULL);
             if (rc) return rc;
+            if (!keep)
+                for (int j = 0; j < k; ++j)
+                    if (B->in[i][j] < 0) fac_free(&B->msg[-(B->in[i][j] + 1)]);
         }
         int p = -1;
         for (int j = 0; j < B->msg[i].nv; ++j) {
@@ -764,7 +776,7 @@ int or_ve_pr(int nvars, const int *card, int nf, const int *off, const int *sv,
     int n = make_order(nvars, &S, evid, order_in, order);
     bte_t B;
     double lr;
-    rc = bte_forward(nvars, &S, order, n, OP_SUM, &B, &lr);
+    rc = bte_forward_k(nvars, &S, order, n, OP_SUM, &B, &lr, 0);
     if (!rc) *logz = lr;
     bte_free(&B);
     free(order);

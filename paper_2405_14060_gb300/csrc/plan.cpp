@@ -1,0 +1,422 @@
+// Contraction-tree planning (host): tree validation, per-node label
+// classification and layouts, complexity accounting, and order search
+// (greedy pair merging, elimination orders, randomised min-fill).
+//
+// A pairwise contraction keeps a label iff the label still occurs outside the
+// subtree or is an output label; every other label of its operands is summed
+// (max-plus: maximised) there (Sec. Tensor networks: "each internal node
+// results from contracting two child tensors and summing out any indices not
+// needed for later operations").
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <numeric>
+#include <queue>
+#include <random>
+#include <set>
+#include <unordered_map>
+
+#include "tn_internal.h"
+
+namespace tn {
+
+double log2_size(const Net &net, const Labels &l) {
+    double s = 0;
+    for (int v : l) s += std::log2((double)net.card[v]);
+    return s;
+}
+
+std::string validate_tree(const Tree &t) {
+    int n = t.nleaves;
+    if (n < 1) return "tree has no leaves";
+    if ((int)t.left.size() != n - 1 || (int)t.right.size() != n - 1)
+        return "tree must have nleaves-1 internal nodes";
+    std::vector<char> used(2 * n - 1, 0);
+    for (int i = 0; i < n - 1; ++i) {
+        int me = n + i;
+        for (int c : {t.left[i], t.right[i]}) {
+            if (c < 0 || c >= me) return "child id out of range or not earlier than its parent";
+            if (used[c]) return "a tensor is contracted twice";
+            used[c] = 1;
+        }
+        if (t.left[i] == t.right[i]) return "a node contracts a tensor with itself";
+    }
+    for (int id = 0; id < 2 * n - 2; ++id)
+        if (!used[id]) return "a tensor is never contracted";
+    return "";
+}
+
+// Sparse label multiset: sorted (label, count) pairs.
+using LCount = std::vector<std::pair<int, int>>;
+
+static LCount merge_counts(const LCount &x, const LCount &y) {
+    LCount r;
+    r.reserve(x.size() + y.size());
+    size_t i = 0, j = 0;
+    while (i < x.size() || j < y.size()) {
+        if (j == y.size() || (i < x.size() && x[i].first < y[j].first)) r.push_back(x[i++]);
+        else if (i == x.size() || y[j].first < x[i].first) r.push_back(y[j++]);
+        else { r.push_back({x[i].first, x[i].second + y[j].second}); ++i; ++j; }
+    }
+    return r;
+}
+
+std::string build_plan(const Net &net, const Tree &tree, Plan &plan) {
+    std::string err = validate_tree(tree);
+    if (!err.empty()) return err;
+    int n = tree.nleaves;
+    if ((int)net.leaf.size() != n) return "tree leaf count does not match the network";
+    plan.net = net;
+    plan.tree = tree;
+    plan.node.assign(2 * n - 1, Node());
+    std::vector<int> total(net.card.size(), 0);
+    std::vector<char> isout(net.card.size(), 0);
+    for (int v : net.out) isout[v] = 1;
+    std::vector<LCount> cnt(2 * n - 1);
+    for (int i = 0; i < n; ++i) {
+        Node &nd = plan.node[i];
+        nd.labels = net.leaf[i];
+        nd.beta = net.leaf_beta.empty() ? false : net.leaf_beta[i];
+        nd.size = 1;
+        for (int v : nd.labels) {
+            nd.size *= net.card[v];
+            total[v]++;
+        }
+        Labels s = nd.labels;
+        std::sort(s.begin(), s.end());
+        for (size_t k = 0; k < s.size(); ++k) {
+            if (k && s[k] == s[k - 1]) return "a leaf repeats a label";
+            cnt[i].push_back({s[k], 1});
+        }
+    }
+    double tot_mul = 0, tot_rw = 0, sc = 0;
+    for (int i = 0; i < n - 1; ++i) {
+        int me = n + i;
+        int x = tree.left[i], y = tree.right[i];
+        Node &nd = plan.node[me];
+        plan.node[x].parent = me;
+        plan.node[y].parent = me;
+        cnt[me] = merge_counts(cnt[x], cnt[y]);
+        // keep rule
+        std::vector<char> keep_l;
+        std::set<int> kept;
+        for (auto &p : cnt[me])
+            if (p.second < total[p.first] || isout[p.first]) kept.insert(p.first);
+        // a = larger operand (its layout is kept), b = smaller
+        int a = x, b = y;
+        if (plan.node[y].size > plan.node[x].size) std::swap(a, b);
+        nd.a = a;
+        nd.b = b;
+        const Labels &la = plan.node[a].labels, &lb = plan.node[b].labels;
+        std::set<int> sa(la.begin(), la.end());
+        // output layout: labels new to C from b (in b's order), then a's kept
+        // labels in a's order
+        nd.labels.clear();
+        for (int v : lb)
+            if (!sa.count(v) && kept.count(v)) nd.labels.push_back(v);
+        for (int v : la)
+            if (kept.count(v)) nd.labels.push_back(v);
+        nd.beta = plan.node[a].beta || plan.node[b].beta;
+        nd.size = 1;
+        for (int v : nd.labels) nd.size *= net.card[v];
+        // eliminated labels in kernel order: a's order, then b-only labels
+        nd.elim.clear();
+        for (int v : la)
+            if (!kept.count(v)) nd.elim.push_back(v);
+        for (int v : lb)
+            if (!sa.count(v) && !kept.count(v)) nd.elim.push_back(v);
+        double mul = 1;
+        for (auto &p : cnt[me]) mul *= net.card[p.first];
+        nd.muladds = mul;
+        tot_mul += mul;
+        tot_rw += (double)plan.node[a].size + (double)plan.node[b].size + (double)nd.size;
+        sc = std::max(sc, std::log2((double)nd.size));
+        // drop eliminated labels from the count list
+        LCount c2;
+        for (auto &p : cnt[me])
+            if (kept.count(p.first)) c2.push_back(p);
+        cnt[me].swap(c2);
+        cnt[x].clear();
+        cnt[y].clear();
+    }
+    plan.root = 2 * n - 2;
+    // depths (root 0)
+    for (int id = 2 * n - 2; id >= 0; --id) {
+        int p = plan.node[id].parent;
+        plan.node[id].depth = p < 0 ? 0 : plan.node[p].depth + 1;
+    }
+    plan.total_muladds = tot_mul;
+    plan.total_rw_entries = tot_rw;
+    plan.tc_log2 = tot_mul > 0 ? std::log2(tot_mul) : 0;
+    plan.rw_log2 = tot_rw > 0 ? std::log2(tot_rw) : 0;
+    plan.sc_log2 = sc;
+    return "";
+}
+
+// ------------------------------------------------------------------ greedy
+//
+// Repeatedly contract the pair of connected tensors (sharing a label) whose
+// result grows least, measured as log2|C| - log2(|A| + |B|); ties go to the
+// pair with the smaller (min id, max id).  Tensors with no shared label are
+// merged last, two smallest first.
+
+namespace {
+struct Frontier {
+    const Net &net;
+    std::vector<Labels> lab;          // sorted labels of each tensor id
+    std::vector<char> alive;
+    std::vector<int> count;           // alive tensors holding each label
+    std::vector<std::set<int>> holders;
+    std::vector<char> isout;
+    explicit Frontier(const Net &n) : net(n) {
+        int L = (int)n.card.size();
+        count.assign(L, 0);
+        holders.assign(L, {});
+        isout.assign(L, 0);
+        for (int v : n.out) isout[v] = 1;
+        for (size_t i = 0; i < n.leaf.size(); ++i) {
+            Labels s = n.leaf[i];
+            std::sort(s.begin(), s.end());
+            lab.push_back(s);
+            alive.push_back(1);
+            for (int v : s) {
+                count[v]++;
+                holders[v].insert((int)i);
+            }
+        }
+    }
+    double lsize(int id) const {
+        double s = 0;
+        for (int v : lab[id]) s += std::log2((double)net.card[v]);
+        return s;
+    }
+    Labels merged(int x, int y) const {
+        Labels u;
+        std::set_union(lab[x].begin(), lab[x].end(), lab[y].begin(), lab[y].end(),
+                       std::back_inserter(u));
+        Labels r;
+        for (int v : u) {
+            int inside = (std::binary_search(lab[x].begin(), lab[x].end(), v) ? 1 : 0) +
+                         (std::binary_search(lab[y].begin(), lab[y].end(), v) ? 1 : 0);
+            if (count[v] > inside || isout[v]) r.push_back(v);
+        }
+        return r;
+    }
+    int merge(int x, int y) {
+        Labels r = merged(x, y);
+        int id = (int)lab.size();
+        for (int v : lab[x]) { count[v]--; holders[v].erase(x); }
+        for (int v : lab[y]) { count[v]--; holders[v].erase(y); }
+        for (int v : r) { count[v]++; holders[v].insert(id); }
+        alive[x] = alive[y] = 0;
+        lab.push_back(r);
+        alive.push_back(1);
+        return id;
+    }
+    std::set<int> neighbours(int id) const {
+        std::set<int> s;
+        for (int v : lab[id])
+            for (int w : holders[v])
+                if (w != id) s.insert(w);
+        return s;
+    }
+};
+
+void record(Tree &t, int n, int x, int y, int id) {
+    (void)n;
+    (void)id;
+    t.left.push_back(x);
+    t.right.push_back(y);
+}
+
+// merge every remaining alive tensor, two smallest first
+void merge_rest(Frontier &F, Tree &t) {
+    using E = std::pair<double, int>;
+    std::priority_queue<E, std::vector<E>, std::greater<E>> pq;
+    for (size_t i = 0; i < F.alive.size(); ++i)
+        if (F.alive[i]) pq.push({F.lsize((int)i), (int)i});
+    while (pq.size() > 1) {
+        int x = pq.top().second; pq.pop();
+        int y = pq.top().second; pq.pop();
+        int id = F.merge(std::min(x, y), std::max(x, y));
+        record(t, 0, std::min(x, y), std::max(x, y), id);
+        pq.push({F.lsize(id), id});
+    }
+}
+}  // namespace
+
+Tree greedy_tree(const Net &net) {
+    Frontier F(net);
+    Tree t;
+    t.nleaves = (int)net.leaf.size();
+    struct Cand {
+        double cost;
+        int x, y;
+        bool operator>(const Cand &o) const {
+            if (cost != o.cost) return cost > o.cost;
+            if (x != o.x) return x > o.x;
+            return y > o.y;
+        }
+    };
+    std::vector<int> ver(2 * net.leaf.size() + 1, 0);
+    struct Entry {
+        Cand c;
+        int vx, vy;
+        bool operator>(const Entry &o) const { return c > o.c; }
+    };
+    std::priority_queue<Entry, std::vector<Entry>, std::greater<Entry>> pq;
+    auto cost = [&](int x, int y) {
+        Labels r = F.merged(x, y);
+        double lc = 0;
+        for (int v : r) lc += std::log2((double)net.card[v]);
+        double la = F.lsize(x), lb = F.lsize(y);
+        double m = std::max(la, lb);
+        double lsum = m + std::log2(std::exp2(la - m) + std::exp2(lb - m));
+        return lc - lsum;
+    };
+    auto push_pair = [&](int x, int y) {
+        if (x > y) std::swap(x, y);
+        pq.push({{cost(x, y), x, y}, ver[x], ver[y]});
+    };
+    for (size_t i = 0; i < net.leaf.size(); ++i)
+        for (int w : F.neighbours((int)i))
+            if ((int)i < w) push_pair((int)i, w);
+    int remaining = (int)net.leaf.size();
+    while (remaining > 1 && !pq.empty()) {
+        Entry e = pq.top();
+        pq.pop();
+        int x = e.c.x, y = e.c.y;
+        if (!F.alive[x] || !F.alive[y] || ver[x] != e.vx || ver[y] != e.vy) continue;
+        std::set<int> nb = F.neighbours(x);
+        for (int w : F.neighbours(y)) nb.insert(w);
+        int id = F.merge(x, y);
+        record(t, 0, x, y, id);
+        --remaining;
+        if ((int)ver.size() <= id) ver.resize(id + 1, 0);
+        nb.erase(x);
+        nb.erase(y);
+        // costs of pairs touching the changed labels' holders are stale
+        std::set<int> touched = nb;
+        for (int w : nb)
+            for (int u : F.neighbours(w)) touched.insert(u);
+        for (int w : touched) ver[w]++;
+        for (int w : touched) {
+            if (!F.alive[w]) continue;
+            for (int u : F.neighbours(w)) push_pair(w, u);
+        }
+        for (int u : F.neighbours(id)) push_pair(id, u);
+    }
+    merge_rest(F, t);
+    return t;
+}
+
+Tree tree_from_elimination(const Net &net, const std::vector<int> &order_in) {
+    Frontier F(net);
+    Tree t;
+    t.nleaves = (int)net.leaf.size();
+    int L = (int)net.card.size();
+    std::vector<char> listed(L, 0);
+    std::vector<int> order;
+    for (int v : order_in)
+        if (v >= 0 && v < L && !listed[v]) { listed[v] = 1; order.push_back(v); }
+    for (int v = 0; v < L; ++v)
+        if (!listed[v]) order.push_back(v);
+    using E = std::pair<double, int>;
+    for (int v : order) {
+        if (F.isout[v]) continue;
+        std::priority_queue<E, std::vector<E>, std::greater<E>> pq;
+        for (int w : F.holders[v]) pq.push({F.lsize(w), w});
+        while (pq.size() > 1) {
+            int x = pq.top().second; pq.pop();
+            int y = pq.top().second; pq.pop();
+            int a = std::min(x, y), b = std::max(x, y);
+            int id = F.merge(a, b);
+            record(t, 0, a, b, id);
+            pq.push({F.lsize(id), id});
+        }
+    }
+    merge_rest(F, t);
+    return t;
+}
+
+// Randomised min-fill (method 1) / min-degree (odd restarts) elimination
+// orders on the interaction graph of the network; ties broken at random.
+static std::vector<int> heuristic_order(const Net &net, bool minfill, std::mt19937_64 &rng) {
+    int L = (int)net.card.size();
+    std::vector<std::vector<char>> adj(L, std::vector<char>(L, 0));
+    std::vector<char> present(L, 0), isout(L, 0);
+    for (int v : net.out) isout[v] = 1;
+    for (auto &lab : net.leaf) {
+        for (int v : lab) present[v] = 1;
+        for (int u : lab)
+            for (int w : lab)
+                if (u != w) adj[u][w] = 1;
+    }
+    std::vector<char> gone(L, 0);
+    std::vector<int> order;
+    std::vector<int> nb;
+    int want = 0;
+    for (int v = 0; v < L; ++v)
+        if (present[v] && !isout[v]) ++want;
+    std::uniform_real_distribution<double> U(0, 1);
+    while ((int)order.size() < want) {
+        int best = -1;
+        double bscore = 0;
+        for (int v = 0; v < L; ++v) {
+            if (!present[v] || isout[v] || gone[v]) continue;
+            nb.clear();
+            for (int u = 0; u < L; ++u)
+                if (!gone[u] && adj[v][u]) nb.push_back(u);
+            double score;
+            if (minfill) {
+                long fill = 0;
+                for (size_t i = 0; i < nb.size(); ++i)
+                    for (size_t j = i + 1; j < nb.size(); ++j)
+                        if (!adj[nb[i]][nb[j]]) ++fill;
+                score = (double)fill;
+            } else {
+                double w = std::log2((double)net.card[v]);
+                for (int u : nb) w += std::log2((double)net.card[u]);
+                score = w;
+            }
+            score += 0.5 * U(rng);   // random tie-breaking (scores are integers / sums)
+            if (best < 0 || score < bscore) { best = v; bscore = score; }
+        }
+        nb.clear();
+        for (int u = 0; u < L; ++u)
+            if (!gone[u] && adj[best][u]) nb.push_back(u);
+        for (int a : nb)
+            for (int c : nb)
+                if (a != c) adj[a][c] = 1;
+        gone[best] = 1;
+        order.push_back(best);
+    }
+    return order;
+}
+
+Tree optimize_tree(const Net &net, int method, int restarts, uint64_t seed) {
+    if (method == 0) return greedy_tree(net);
+    std::mt19937_64 rng(seed);
+    Tree best;
+    double bsc = 1e300, btc = 1e300;
+    if (restarts < 1) restarts = 1;
+    for (int r = 0; r < restarts; ++r) {
+        std::vector<int> order = heuristic_order(net, (r % 2) == 0, rng);
+        Tree t = tree_from_elimination(net, order);
+        Plan p;
+        if (!build_plan(net, t, p).empty()) continue;
+        if (p.sc_log2 < bsc - 1e-9 || (std::fabs(p.sc_log2 - bsc) < 1e-9 && p.tc_log2 < btc)) {
+            bsc = p.sc_log2;
+            btc = p.tc_log2;
+            best = t;
+        }
+    }
+    Tree g = greedy_tree(net);
+    Plan pg;
+    if (build_plan(net, g, pg).empty() &&
+        (pg.sc_log2 < bsc - 1e-9 || (std::fabs(pg.sc_log2 - bsc) < 1e-9 && pg.tc_log2 < btc)))
+        best = g;
+    return best;
+}
+
+}  // namespace tn

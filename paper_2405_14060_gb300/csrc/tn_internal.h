@@ -1,0 +1,60 @@
+// Internal data structures of libtn: tensor networks, contraction trees and
+// per-node plans (host side).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "tn.h"
+
+namespace tn {
+
+using Labels = std::vector<int>;
+
+// A tensor network (Lambda, T, V0) (Def. "Tensor Network"): leaf label lists
+// in storage order (last label fastest), label sizes, output labels V0.  A
+// leaf may also carry the evidence-batch label (always outermost), which is
+// kept to the root.
+struct Net {
+    std::vector<int> card;            // size of every label
+    std::vector<Labels> leaf;         // labels of each leaf
+    std::vector<char> leaf_beta;      // leaf carries the batch label
+    Labels out;                       // V0
+};
+
+// Binary contraction tree over nleaves leaves: internal node i has id
+// nleaves + i and children left[i], right[i] (Sec. Tensor networks).
+struct Tree {
+    int nleaves = 0;
+    std::vector<int> left, right;
+};
+
+// Plan of one tensor of the tree (leaf or internal node).
+struct Node {
+    Labels labels;        // storage order, batch label excluded
+    bool beta = false;    // carries the batch label (outermost dimension)
+    int64_t size = 1;     // entries per batch item
+    int a = -1, b = -1;   // operands: a is the larger (its layout is kept)
+    Labels elim;          // labels summed/maximised here, in kernel K order
+    double muladds = 0;   // prod over the union of operand labels (per item)
+    int parent = -1;
+    int depth = 0;
+};
+
+struct Plan {
+    Net net;
+    Tree tree;
+    std::vector<Node> node;           // leaves first, then internal nodes
+    int root = -1;
+    double tc_log2 = 0, sc_log2 = 0, rw_log2 = 0;
+    double total_muladds = 0, total_rw_entries = 0;
+};
+
+std::string validate_tree(const Tree &t);
+std::string build_plan(const Net &net, const Tree &tree, Plan &plan);
+Tree greedy_tree(const Net &net);
+Tree tree_from_elimination(const Net &net, const std::vector<int> &order);
+Tree optimize_tree(const Net &net, int method, int restarts, uint64_t seed);
+double log2_size(const Net &net, const Labels &l);
+
+}  // namespace tn

@@ -1,0 +1,282 @@
+"""Thin ctypes binding of libtn (include/tn.h).
+
+Argument marshalling only: every computation runs in libtn's CUDA kernels.
+There is no fallback -- importing the binding without a built libtn raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+TN_FP64, TN_FP32, TN_TF32, TN_BF16 = 0, 1, 2, 3
+PRECS = {"fp64": TN_FP64, "fp32": TN_FP32, "tf32": TN_TF32, "bf16": TN_BF16}
+STATUS = {0: "TN_OK", 1: "TN_E_ARG", 2: "TN_E_PARSE", 3: "TN_E_ORDER", 4: "TN_E_OOM",
+          5: "TN_E_CUDA", 6: "TN_E_TIMEOUT", 7: "TN_E_UNSUPPORTED"}
+
+# Every symbol include/tn.h declares (checked by the CPU test suite).
+EXPORTS = ["tn_load_model", "tn_load_model_arrays", "tn_free_model", "tn_set_order",
+           "tn_tree_from_elimination", "tn_optimize_order", "tn_tree_stats", "tn_pr",
+           "tn_mar", "tn_map", "tn_mmap", "tn_sample", "tn_pr_dev", "tn_mar_dev",
+           "tn_last_device_ms", "tn_last_launch_count", "tn_last_error", "tn_contract_dev"]
+
+
+class TNError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_int64),
+                ("max_slices", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("cuda_stream", ctypes.c_void_p)]
+
+
+_lib = None
+LIB_PATH = _build.LIB
+
+
+def lib():
+    """Load libtn.so (built in-tree by __graft_entry__.build() / build.py)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libtn.so is not built ({LIB_PATH}); run "
+                              "python -c 'import __graft_entry__ as g; g.build()'")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, I64, D, U64 = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double,
+                             ctypes.c_uint64)
+        sig = {
+            "tn_load_model": [ctypes.c_char_p, P],
+            "tn_load_model_arrays": [I, P, I, P, P, P, P],
+            "tn_set_order": [P, I, P, P, I, P],
+            "tn_tree_from_elimination": [P, I, P, P, P],
+            "tn_optimize_order": [P, I, I, U64, P, P],
+            "tn_tree_stats": [P, I, I, P],
+            "tn_pr": [P, I, P, P, P],
+            "tn_mar": [P, I, P, P, P, P],
+            "tn_map": [P, P, P, P, P],
+            "tn_mmap": [P, P, I, P, P, P, P],
+            "tn_sample": [P, P, U64, I64, P, P],
+            "tn_pr_dev": [P, I, P, P, I, P, P],
+            "tn_mar_dev": [P, I, P, P, I, P, P, P, P],
+            "tn_contract_dev": [I, P, I, P, P, I, P, P, I, P, P, I, I, I, P, P],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.tn_free_model.argtypes = [P]
+        L.tn_free_model.restype = None
+        L.tn_last_error.restype = ctypes.c_char_p
+        L.tn_last_device_ms.argtypes = [P]
+        L.tn_last_device_ms.restype = D
+        L.tn_last_launch_count.argtypes = [P]
+        L.tn_last_launch_count.restype = I64
+        _lib = L
+    return _lib
+
+
+def _ck(st: int):
+    if st != 0:
+        raise TNError(st, lib().tn_last_error().decode())
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _opts(prec="fp64", budget=0, stream=None) -> Options:
+    o = Options()
+    o.prec = PRECS[prec] if isinstance(prec, str) else int(prec)
+    o.hbm_budget_bytes = int(budget)
+    o.max_slices = 0
+    o.autotune = 0
+    o.cuda_stream = stream
+    return o
+
+
+class Model:
+    """A graphical model held by libtn (one tn_model)."""
+
+    def __init__(self, handle, nvars, card, nfactors, table_sizes):
+        self._h = handle
+        self.nvars = nvars
+        self.card = np.asarray(card, np.int32)
+        self.nfactors = nfactors
+        self.table_sizes = np.asarray(table_sizes, np.int64)
+
+    @property
+    def nleaves(self):
+        return self.nfactors + self.nvars
+
+    @classmethod
+    def from_arrays(cls, card, scopes, tables) -> "Model":
+        card = np.ascontiguousarray(card, np.int32)
+        off = np.zeros(len(scopes) + 1, np.int32)
+        for i, s in enumerate(scopes):
+            off[i + 1] = off[i] + len(s)
+        sv = (np.ascontiguousarray(np.concatenate([np.asarray(s, np.int32) for s in scopes]))
+              if scopes else np.zeros(1, np.int32))
+        tb = (np.ascontiguousarray(np.concatenate([np.asarray(t, np.float64) for t in tables]))
+              if tables else np.zeros(1))
+        h = ctypes.c_void_p()
+        _ck(lib().tn_load_model_arrays(len(card), _ptr(card), len(scopes), _ptr(off), _ptr(sv),
+                                       _ptr(tb), ctypes.byref(h)))
+        return cls(h, len(card), card, len(scopes), [len(t) for t in tables])
+
+    @classmethod
+    def from_synth(cls, m) -> "Model":
+        return cls.from_arrays(m.card, m.scopes, m.tables)
+
+    @classmethod
+    def from_uai(cls, path: str) -> "Model":
+        h = ctypes.c_void_p()
+        _ck(lib().tn_load_model(path.encode(), ctypes.byref(h)))
+        # read back sizes from the file header for convenience
+        with open(path) as f:
+            toks = f.read().split()
+        n = int(toks[1])
+        card = [int(t) for t in toks[2:2 + n]]
+        nf = int(toks[2 + n])
+        p = 3 + n
+        sizes = []
+        for _ in range(nf):
+            k = int(toks[p]); p += 1
+            sizes.append(int(np.prod([card[int(v)] for v in toks[p:p + k]])))
+            p += k
+        return cls(h, n, card, nf, sizes)
+
+    def __del__(self):
+        try:
+            if self._h:
+                lib().tn_free_model(self._h)
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ orders
+    def set_order(self, left=None, right=None, slice_vars: Sequence[int] = ()):
+        sl = np.ascontiguousarray(slice_vars, np.int32) if len(slice_vars) else None
+        if left is None:
+            _ck(lib().tn_set_order(self._h, 0, None, None, 0, None))
+            return
+        l = np.ascontiguousarray(left, np.int32)
+        r = np.ascontiguousarray(right, np.int32)
+        _ck(lib().tn_set_order(self._h, len(l), _ptr(l), _ptr(r),
+                               0 if sl is None else len(sl), None if sl is None else _ptr(sl)))
+
+    def tree_from_elimination(self, order):
+        o = np.ascontiguousarray(order, np.int32)
+        l = np.zeros(self.nleaves - 1, np.int32)
+        r = np.zeros(self.nleaves - 1, np.int32)
+        _ck(lib().tn_tree_from_elimination(self._h, len(o), _ptr(o), _ptr(l), _ptr(r)))
+        return l, r
+
+    def optimize_order(self, method=1, restarts=8, seed=0):
+        l = np.zeros(self.nleaves - 1, np.int32)
+        r = np.zeros(self.nleaves - 1, np.int32)
+        _ck(lib().tn_optimize_order(self._h, method, restarts, seed, _ptr(l), _ptr(r)))
+        return l, r
+
+    def tree_stats(self, batch=1, prec="fp64"):
+        out = np.zeros(6)
+        _ck(lib().tn_tree_stats(self._h, batch, PRECS[prec], _ptr(out)))
+        return {"tc": out[0], "sc": out[1], "rw": out[2], "nodes": int(out[3]),
+                "flops": out[4], "bytes": out[5]}
+
+    # ------------------------------------------------------------ tasks
+    def _evid(self, evid, batch=None):
+        if evid is None:
+            b = 1 if batch is None else batch
+            return np.full((b, self.nvars), -1, np.int32)
+        e = np.ascontiguousarray(evid, np.int32)
+        return e.reshape(-1, self.nvars)
+
+    def pr(self, evid=None, prec="fp64", budget=0):
+        e = self._evid(evid)
+        out = np.zeros(e.shape[0])
+        o = _opts(prec, budget)
+        _ck(lib().tn_pr(self._h, e.shape[0], _ptr(e), ctypes.byref(o), _ptr(out)))
+        return out
+
+    def mar(self, evid=None, prec="fp64", budget=0):
+        e = self._evid(evid)
+        lz = np.zeros(e.shape[0])
+        marg = np.zeros((e.shape[0], int(self.card.sum())))
+        o = _opts(prec, budget)
+        _ck(lib().tn_mar(self._h, e.shape[0], _ptr(e), ctypes.byref(o), _ptr(lz), _ptr(marg)))
+        return lz, marg
+
+    def split(self, marg_row):
+        out, p = [], 0
+        for c in self.card:
+            out.append(marg_row[p:p + int(c)])
+            p += int(c)
+        return out
+
+    def map(self, evid=None, prec="fp64"):
+        e = self._evid(evid)
+        x = np.zeros(self.nvars, np.int32)
+        lp = ctypes.c_double()
+        o = _opts(prec)
+        _ck(lib().tn_map(self._h, _ptr(e[0]), ctypes.byref(o), _ptr(x), ctypes.byref(lp)))
+        return x, lp.value
+
+    def mmap(self, query, evid=None, prec="fp64"):
+        e = self._evid(evid)
+        q = np.ascontiguousarray(query, np.int32)
+        x = np.zeros(len(q), np.int32)
+        lp = ctypes.c_double()
+        o = _opts(prec)
+        _ck(lib().tn_mmap(self._h, _ptr(e[0]), len(q), _ptr(q), ctypes.byref(o), _ptr(x),
+                          ctypes.byref(lp)))
+        return x, lp.value
+
+    def sample(self, n, seed=0, evid=None, prec="fp64"):
+        e = self._evid(evid)
+        out = np.zeros((n, self.nvars), np.int8)
+        o = _opts(prec)
+        _ck(lib().tn_sample(self._h, _ptr(e[0]), seed, n, ctypes.byref(o), _ptr(out)))
+        return out
+
+    # ------------------------------------------------- device-pointer forms
+    def pr_dev(self, evid, logz, tables=None, tables_are_log=False, prec="fp32", stream=None):
+        """evid, logz (and tables) are torch CUDA tensors (int32 / float64)."""
+        o = _opts(prec, 0, stream)
+        _ck(lib().tn_pr_dev(self._h, int(evid.shape[0]), evid.data_ptr(),
+                            None if tables is None else tables.data_ptr(),
+                            1 if tables_are_log else 0, ctypes.byref(o), logz.data_ptr()))
+
+    def mar_dev(self, evid, logz, marg, grad=None, tables=None, tables_are_log=False,
+                prec="fp32", stream=None):
+        o = _opts(prec, 0, stream)
+        _ck(lib().tn_mar_dev(self._h, int(evid.shape[0]), evid.data_ptr(),
+                             None if tables is None else tables.data_ptr(),
+                             1 if tables_are_log else 0, ctypes.byref(o), logz.data_ptr(),
+                             marg.data_ptr(), None if grad is None else grad.data_ptr()))
+
+    def last_device_ms(self) -> float:
+        return float(lib().tn_last_device_ms(self._h))
+
+    def last_launch_count(self) -> int:
+        return int(lib().tn_last_launch_count(self._h))
+
+
+def contract_dev(sizes, la, A, lb, B, lc, C, semiring=0, argmax=None, prec="fp32",
+                 stream=None):
+    """One pairwise contraction on torch CUDA tensors (float64 or float32)."""
+    import torch
+    dtype = 0 if A.dtype == torch.float64 else 1
+    sz = np.ascontiguousarray(sizes, np.int32)
+    a = np.ascontiguousarray(la, np.int32)
+    b = np.ascontiguousarray(lb, np.int32)
+    c = np.ascontiguousarray(lc, np.int32)
+    _ck(lib().tn_contract_dev(len(sz), _ptr(sz), len(a), _ptr(a), A.data_ptr(), len(b), _ptr(b),
+                              B.data_ptr(), len(c), _ptr(c) if len(c) else None, C.data_ptr(),
+                              semiring, dtype, PRECS[prec],
+                              None if argmax is None else argmax.data_ptr(), stream))

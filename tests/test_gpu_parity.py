@@ -1,0 +1,212 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances: FP64 log Z within 1e-10 absolute and marginals within 1e-10;
+FP32 / TF32 / BF16 log Z within 1e-4 relative (|dlogZ| / |logZ|) and
+marginals within 1e-3 absolute; MPE / MMAP assignments bit-exact (continuous
+random tables make ties vanish; the oracle's certificate below guards it).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import con
+from paper_2405_14060_gb300 import synth, tn
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+
+
+def _marg_close(M, marg_row, ref, atol):
+    for v, (a, b) in enumerate(zip(M.split(marg_row), ref)):
+        assert np.max(np.abs(a - b)) <= atol, (v, a, b)
+
+
+SMALL = [
+    ("grid4", lambda: synth.grid_ising(4, 3)),
+    ("rand11", lambda: synth.random_markov(11, 14, 3, 5, cards=(2, 3))),
+    ("bn14", lambda: synth.bayes_net(14, 9)),
+    ("chain12", lambda: synth.chain_model(12, [2, 3, 4] * 4, 2)),
+]
+
+
+@pytest.mark.parametrize("name,mk", SMALL)
+@pytest.mark.parametrize("method", [0, 1])
+def test_pr_mar_small_fp64(name, mk, method):
+    m = mk()
+    M = tn.Model.from_synth(m)
+    M.set_order(*M.optimize_order(method, 4, 3))
+    rng = np.random.default_rng(1)
+    ev = synth.random_evidence(m, 0.2, rng)
+    lz_ref, marg_ref = oracle.brute_mar(m, ev)
+    lz, marg = M.mar(ev, prec="fp64")
+    assert abs(lz[0] - lz_ref) < 1e-10
+    assert abs(M.pr(ev, prec="fp64")[0] - lz_ref) < 1e-10
+    _marg_close(M, marg[0], marg_ref, 1e-10)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
+def test_pr_mar_small_reduced(prec):
+    m = synth.grid_ising(4, 5)
+    M = tn.Model.from_synth(m)
+    lz_ref, marg_ref = oracle.brute_mar(m)
+    lz, marg = M.mar(prec=prec)
+    assert abs(lz[0] - lz_ref) <= 1e-4 * abs(lz_ref)
+    _marg_close(M, marg[0], marg_ref, 1e-3)
+
+
+def test_batched_evidence_matches_per_item():
+    m = synth.random_markov(10, 13, 3, 8, cards=(2, 3))
+    M = tn.Model.from_synth(m)
+    ev = synth.evidence_batch(m, 5, 0.3, 11)
+    lz, marg = M.mar(ev, prec="fp64")
+    for b in range(ev.shape[0]):
+        lzr, mr = oracle.brute_mar(m, ev[b])
+        assert abs(lz[b] - lzr) < 1e-10
+        _marg_close(M, marg[b], mr, 1e-10)
+    lz32 = M.pr(ev, prec="fp32")
+    np.testing.assert_allclose(lz32, lz, rtol=1e-4)
+
+
+def test_impossible_evidence():
+    m = synth.chain_model(4, [2, 2, 2, 2], 1)
+    m.tables[0] = np.array([0.0, 1.0])          # x0 = 0 has zero weight
+    M = tn.Model.from_synth(m)
+    ev = np.array([0, -1, -1, -1], np.int32)
+    assert M.pr(ev)[0] == -np.inf
+    with pytest.raises(tn.TNError):
+        M.mar(ev)
+    with pytest.raises(tn.TNError):
+        M.map(ev)
+
+
+def test_workload1_full():
+    w = synth.workload(1)
+    m = w.model
+    M = tn.Model.from_synth(m)          # greedy order (the default)
+    lz_ref, marg_ref = oracle.ve_mar(m)
+    lz, marg = M.mar(prec="fp64")
+    assert abs(lz[0] - lz_ref) < 1e-10
+    _marg_close(M, marg[0], marg_ref, 1e-10)
+    for prec in ("fp32", "tf32", "bf16"):
+        lz2, marg2 = M.mar(prec=prec)
+        assert abs(lz2[0] - lz_ref) <= 1e-4 * abs(lz_ref), prec
+        _marg_close(M, marg2[0], marg_ref, 1e-3)
+
+
+def test_map_small_and_workload3():
+    for name, mk in SMALL:
+        m = mk()
+        M = tn.Model.from_synth(m)
+        ev = synth.random_evidence(m, 0.2, np.random.default_rng(4))
+        xb, lb = oracle.brute_map(m, ev)
+        for prec in ("fp64", "fp32"):
+            x, lp = M.map(ev, prec=prec)
+            np.testing.assert_array_equal(x, xb)
+            assert abs(lp - lb) < (1e-9 if prec == "fp64" else 1e-3 * max(1, abs(lb)))
+    w = synth.workload(3)
+    m, ev = w.model, w.evid[0]
+    xo, lo = oracle.ve_map(m, ev)
+    M = tn.Model.from_synth(m)
+    for prec in ("fp64", "fp32"):
+        x, lp = M.map(ev, prec=prec)
+        np.testing.assert_array_equal(x, xo)
+        assert abs(oracle.log_weight(m, x) - lo) < 1e-9
+
+
+def test_mmap_small_and_workload3():
+    for seed in range(3):
+        m = synth.bayes_net(14, 40 + seed)
+        rng = np.random.default_rng(seed)
+        ev = synth.random_evidence(m, 0.2, rng)
+        q = synth.mmap_query(m, ev, 0.4, rng)
+        xb, lb = oracle.brute_mmap(m, q, ev)
+        M = tn.Model.from_synth(m)
+        for prec in ("fp64", "fp32"):
+            x, lp = M.mmap(q, ev, prec=prec)
+            np.testing.assert_array_equal(x, xb)
+            assert abs(lp - lb) < (1e-9 if prec == "fp64" else 1e-3)
+    w = synth.workload(3)
+    xo, lo = oracle.ve_mmap(w.model, w.query, w.evid[0])
+    M = tn.Model.from_synth(w.model)
+    for prec in ("fp64", "fp32"):
+        x, lp = M.mmap(w.query, w.evid[0], prec=prec)
+        np.testing.assert_array_equal(x, xo)
+        assert abs(lp - lo) < (1e-8 if prec == "fp64" else 1e-3)
+
+
+def test_sampling_small_chi_square():
+    m = synth.random_markov(7, 8, 3, 5, cards=(2, 3))
+    ev = np.full(m.nvars, -1, np.int32)
+    ev[2] = 1
+    joint = oracle.brute_joint(m, ev)
+    M = tn.Model.from_synth(m)
+    n = 200000
+    s = M.sample(n, seed=7, evid=ev, prec="fp64")
+    assert np.all(s[:, 2] == 1)
+    free = [v for v in range(m.nvars) if ev[v] < 0]
+    idx = np.zeros(n, np.int64)
+    for v in free:
+        idx = idx * int(m.card[v]) + s[:, v]
+    emp = np.bincount(idx, minlength=len(joint))
+    expc = joint * n
+    keep = expc >= 5
+    chi2 = np.sum((emp[keep] - expc[keep]) ** 2 / expc[keep])
+    dof = int(keep.sum()) - 1
+    assert chi2 < dof + 6 * np.sqrt(2 * dof), (chi2, dof)
+    s2 = M.sample(1000, seed=7, evid=ev, prec="fp64")
+    np.testing.assert_array_equal(s2, s[:1000])     # counter-based: reproducible
+
+
+# ------------------------------------------------------ pairwise contraction
+
+CASES = [
+    # sizes, labels A, labels B, labels C
+    ([3, 4, 5], [0, 1], [1, 2], [0, 2]),                 # matmul
+    ([2, 3, 2, 3, 2, 2], [0, 3], [3], [0]),              # matvec
+    ([2] * 12, [0, 1, 2, 3, 4, 5, 6, 7, 8, 9], [9, 10, 11], [10, 0, 1, 2, 3, 4, 5, 6, 7, 8, 11]),
+    ([3, 2, 4, 5, 2], [0, 1, 2], [2, 3, 1], [3, 0, 1]),  # batch label 1
+    ([2] * 16, list(range(16)), list(range(16)), []),   # full trace, split-K
+    ([5, 7, 3, 2], [0, 1, 2], [3], [0, 3]),              # labels summed in one operand
+]
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+@pytest.mark.parametrize("dtype", ["float64", "float32"])
+def test_contract_dev_matches_definition(case, dtype):
+    sizes, la, lb, lc = CASES[case]
+    rng = np.random.default_rng(case)
+    A = rng.random([sizes[v] for v in la])
+    B = rng.random([sizes[v] for v in lb])
+    ref = con.con_dense([tuple(la), tuple(lb)], [A, B], tuple(lc))
+    dt = getattr(torch, dtype)
+    tA = torch.tensor(A, dtype=dt, device="cuda").contiguous()
+    tB = torch.tensor(B, dtype=dt, device="cuda").contiguous()
+    tC = torch.zeros([sizes[v] for v in lc] or [1], dtype=dt, device="cuda")
+    tn.contract_dev(sizes, la, tA, lb, tB, lc, tC)
+    got = tC.cpu().numpy().reshape(np.shape(ref))
+    tol = 1e-12 if dtype == "float64" else 2e-5
+    np.testing.assert_allclose(got, ref, rtol=tol, atol=0)
+    # tropical
+    ref_v, ref_i = con.tcon_dense([tuple(la), tuple(lb)], [np.log(A), np.log(B)], tuple(lc))
+    tA = torch.tensor(np.log(A), dtype=dt, device="cuda").contiguous()
+    tB = torch.tensor(np.log(B), dtype=dt, device="cuda").contiguous()
+    am = torch.zeros(tC.numel(), dtype=torch.int32, device="cuda")
+    tn.contract_dev(sizes, la, tA, lb, tB, lc, tC, semiring=1, argmax=am)
+    # argmax order: labels of A not in C (A's order), then B-only labels
+    elim = [v for v in la if v not in lc] + [v for v in lb if v not in lc and v not in la]
+    elim_ref = [v for v in dict.fromkeys(la + lb) if v not in lc]
+    assert elim == elim_ref
+    gv = tC.cpu().numpy().reshape(np.shape(ref_v))
+    if dtype == "float64":
+        np.testing.assert_allclose(gv, ref_v, rtol=0, atol=1e-12)
+        np.testing.assert_array_equal(am.cpu().numpy().reshape(np.shape(ref_i)), ref_i)
+    else:
+        np.testing.assert_allclose(gv, ref_v, rtol=0, atol=1e-4 * max(1, np.abs(ref_v).max()))

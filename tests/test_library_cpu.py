@@ -1,0 +1,139 @@
+"""Host-side checks of libtn that need no GPU: the library loads and exports
+every symbol include/tn.h declares, input validation, UAI I/O, tree
+validation, and the planner's complexity accounting against an independent
+recomputation of the keep rule."""
+import os
+import re
+import tempfile
+
+import numpy as np
+import pytest
+
+from paper_2405_14060_gb300 import build, synth, tn
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    build.build()
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "tn.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(tn_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol():
+    L = tn.lib()
+    names = _declared()
+    assert names, "no declarations found"
+    for n in names:
+        assert hasattr(L, n), n
+    assert sorted(tn.EXPORTS) == names
+
+
+def test_model_validation_errors():
+    with pytest.raises(tn.TNError) as e:
+        tn.Model.from_arrays([2, 0], [[0, 1]], [np.ones(0)])
+    assert e.value.status == 1
+    with pytest.raises(tn.TNError):
+        tn.Model.from_arrays([2, 2], [[0, 2]], [np.ones(4)])
+    with pytest.raises(tn.TNError):
+        tn.Model.from_arrays([2, 2], [[0, 0]], [np.ones(4)])
+    with pytest.raises(tn.TNError):
+        tn.Model.from_arrays([2, 2], [[0, 1]], [np.array([1.0, -1.0, 1.0, 1.0])])
+    with pytest.raises(tn.TNError):
+        tn.Model.from_arrays([2, 2], [[0, 1]], [np.array([1.0, np.inf, 1.0, 1.0])])
+
+
+def test_uai_roundtrip_and_parse_errors():
+    m = synth.bayes_net(10, 3)
+    with tempfile.TemporaryDirectory() as d:
+        p = os.path.join(d, "m.uai")
+        synth.write_uai(m, p)
+        M = tn.Model.from_uai(p)
+        assert M.nvars == m.nvars and M.nfactors == m.nfactors
+        m2 = synth.read_uai(p)
+        for a, b in zip(m.tables, m2.tables):
+            np.testing.assert_array_equal(a, b)
+        bad = os.path.join(d, "bad.uai")
+        with open(bad, "w") as f:
+            f.write("MARKOV\n2\n2 2\n1\n2 0 1\n3\n1 1 1\n")
+        with pytest.raises(tn.TNError) as e:
+            tn.Model.from_uai(bad)
+        assert e.value.status == 2
+        with open(bad, "w") as f:
+            f.write("GRAPH\n")
+        with pytest.raises(tn.TNError) as e:
+            tn.Model.from_uai(bad)
+        assert e.value.status == 2
+
+
+def test_tree_validation():
+    m = synth.grid_ising(3, 1)
+    M = tn.Model.from_synth(m)
+    n = M.nleaves
+    l, r = M.optimize_order(0)
+    M.set_order(l, r)
+    bad_l = l.copy()
+    bad_l[-1] = bad_l[0]                    # a tensor contracted twice
+    with pytest.raises(tn.TNError) as e:
+        M.set_order(bad_l, r)
+    assert e.value.status == 3
+    bad_r = r.copy()
+    bad_r[0] = n + 5                        # child not earlier than its parent
+    with pytest.raises(tn.TNError):
+        M.set_order(l, bad_r)
+    with pytest.raises(tn.TNError):
+        M.set_order(l[:-1], r[:-1])         # too few nodes
+
+
+def _keep_rule_stats(m, left, right):
+    """Independent recomputation: a label is kept at a node iff some leaf
+    outside the node's subtree holds it (output labels are empty)."""
+    leaves = [set(map(int, s)) for s in m.scopes] + [{v} for v in range(m.nvars)]
+    n = len(leaves)
+    sub = [{i} for i in range(n)]
+    labels = [set(s) for s in leaves]
+    muladds, sc = 0, 0
+    for i, (a, b) in enumerate(zip(left, right)):
+        me = n + i
+        sub.append(sub[a] | sub[b])
+        outside = set()
+        for j in range(n):
+            if j not in sub[me]:
+                outside |= leaves[j]
+        u = labels[a] | labels[b]
+        labels.append({v for v in u if v in outside})
+        muladds += int(np.prod([m.card[v] for v in u]))
+        sc = max(sc, int(np.prod([m.card[v] for v in labels[me]])))
+    return np.log2(muladds), np.log2(sc)
+
+
+@pytest.mark.parametrize("method", [0, 1])
+def test_tree_stats_match_keep_rule(method):
+    m = synth.random_markov(9, 12, 3, 4, cards=(2, 3))
+    M = tn.Model.from_synth(m)
+    l, r = M.optimize_order(method, 4, 7)
+    M.set_order(l, r)
+    st = M.tree_stats(1, "fp64")
+    tc, sc = _keep_rule_stats(m, l, r)
+    assert abs(st["tc"] - tc) < 1e-9
+    assert abs(st["sc"] - sc) < 1e-9
+    assert st["nodes"] == M.nleaves - 1
+
+
+def test_elimination_tree_is_valid_and_deterministic():
+    m = synth.grid_ising(6, 2)
+    M = tn.Model.from_synth(m)
+    l1, r1 = M.tree_from_elimination(np.arange(m.nvars))
+    l2, r2 = M.tree_from_elimination(np.arange(m.nvars))
+    np.testing.assert_array_equal(l1, l2)
+    M.set_order(l1, r1)
+    assert M.tree_stats()["sc"] == 6.0      # a row sweep keeps one row (+1 label)  of 6
+    g1 = M.optimize_order(0)
+    g2 = M.optimize_order(0)
+    np.testing.assert_array_equal(g1[0], g2[0])
