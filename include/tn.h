@@ -26,11 +26,12 @@
  *   - Evidence vectors are int32 [nvars]: observed value, or -1 if free.
  *   - Logarithms are natural.
  *   - Output buffers are owned by the caller.  Functions without the _dev
- *     suffix take HOST pointers and copy through the library's stream; the
- *     _dev variants take DEVICE pointers and enqueue on opts->cuda_stream
- *     (0 = the legacy default stream) and return once the work is enqueued
- *     and complete (they synchronise the stream before returning, so the
- *     outputs are valid on return).
+ *     suffix take HOST pointers and copy through the library's stream.  The
+ *     _dev variants take DEVICE pointers.  With opts->cuda_stream set they
+ *     only enqueue their work on that stream (outputs are valid once the
+ *     stream reaches that point; a device-side wait that gave up is reported
+ *     by the next synchronous call); without it they run on the model's own
+ *     stream and synchronise before returning.
  *   - No exception crosses the ABI.  Every call returns a tn_status; on
  *     failure tn_last_error() describes the cause (thread-local string, valid
  *     until the next call on the same thread).
@@ -198,6 +199,23 @@ double tn_last_device_ms(const tn_model *m);
 /* Number of kernel launches the last task issued (graph nodes counted). */
 int64_t tn_last_launch_count(const tn_model *m);
 
+/* Profile one PR (task 0) or PR + MAR (task 1) pass kernel by kernel (each
+ * launch timed with CUDA events on the model's stream, outside any graph),
+ * averaged over `reps` passes.  out[8][4] per kernel class: milliseconds,
+ * launches, algorithmic FLOPs (2 per multiply-add of a contraction) and
+ * algorithmic bytes (operands and result once).  Classes: 0 leaves and
+ * finalisation (not timed, reported as 0), 1 streaming absorb, 2 streaming
+ * reduction (or split-K), 3 tcgen05 GEMM, 4 CUDA-core GEMM, 5 operand
+ * preparation / scatter, 6 generic strided contraction, 7 unused. */
+tn_status tn_profile(tn_model *m, int task, int batch, const int32_t *evid,
+                     const tn_options *opts, int reps, double *out);
+
+/* Like tn_profile for one pass, but per launch in launch order:
+ * steps[i][4] = class, milliseconds, algorithmic FLOPs, algorithmic bytes
+ * for i < min(cap, *nsteps); *nsteps receives the number of launches. */
+tn_status tn_profile_steps(tn_model *m, int task, int batch, const int32_t *evid,
+                           const tn_options *opts, int cap, double *steps, int *nsteps);
+
 const char *tn_last_error(void);
 
 /* ---------------------------------------------------- pairwise contraction */
@@ -213,9 +231,14 @@ const char *tn_last_error(void);
  *               eliminated label slowest, in the order: labels of A not in
  *               C in A's order, then labels of B in neither A nor C in B's
  *               order) of the first maximising assignment.
- * dtype: 0 = double, 1 = float.  prec selects the kernel family for float
- * (TN_FP32, TN_TF32, TN_BF16).  No rescaling is applied.  The call
- * allocates its scratch memory from the library and synchronises `stream`.
+ * dtype: 0 = double, 1 = float.  A sum-product contraction whose row, column
+ * and summed label groups each hold at least 64 entries (and with no label
+ * summed inside one operand alone) runs as a batched GEMM: TN_TF32 / TN_BF16
+ * on tcgen05 tensor cores (float data only), TN_FP32 / TN_FP64 on a CUDA-core
+ * tiled GEMM; everything else runs on the strided contraction kernels.  No
+ * rescaling is applied.  The call allocates its scratch memory (operand
+ * workspaces, split-K partial sums) stream-ordered from the CUDA memory pool
+ * and synchronises `cuda_stream` before returning.
  */
 tn_status tn_contract_dev(int nlabels, const int *sizes,
                           int na, const int *labels_a, const void *A,

@@ -172,6 +172,19 @@ def ve_pr(model, evid=None, order=None) -> float:
     return out.value
 
 
+def ve_pr_prefix(model, order, nelim, evid=None):
+    """Eliminate only the first ``nelim`` variables of ``order`` (a bounded
+    sample of a PR elimination).  Returns (work of the prefix, work of the
+    full order), both as the symbolic count of bucket entries visited."""
+    m, e = _M(model), _ev(model, evid)
+    o = np.full(m.n + 1, -1, np.int32)
+    o[:len(order)] = order
+    wp, wf = ctypes.c_double(), ctypes.c_double()
+    _check(_load().or_ve_pr_prefix(*m.args(), _p(e), _p(o), ctypes.c_int(nelim),
+                                   ctypes.byref(wp), ctypes.byref(wf)), "ve_pr_prefix")
+    return wp.value, wf.value
+
+
 def ve_mar(model, evid=None):
     m, e = _M(model), _ev(model, evid)
     out = ctypes.c_double()

@@ -623,9 +623,14 @@ static int bte_forward(int nvars, sliced_t *S, const int *order, int n, int op,
     return bte_forward_k(nvars, S, order, n, op, B, lroot, 1);
 }
 
-/* keep = 0 frees every message once its receiving bucket has used it. */
+/* keep = 0 frees every message once its receiving bucket has used it;
+ * keep = -1 additionally allows variables outside `order` (a partial
+ * elimination): functions holding none of the ordered variables are left
+ * aside and the messages over them discarded. */
 static int bte_forward_k(int nvars, sliced_t *S, const int *order, int n, int op,
                          bte_t *B, double *lroot, int keep) {
+    const int partial = keep < 0;
+    if (partial) keep = 0;
     memset(B, 0, sizeof(*B));
     B->n = n;
     B->var = (int *)malloc(sizeof(int) * (size_t)(n ? n : 1));
@@ -645,6 +650,7 @@ static int bte_forward_k(int nvars, sliced_t *S, const int *order, int n, int op
             if (p >= 0 && (b < 0 || p < b)) b = p;
         }
         if (b >= 0) bte_add(B, b, f);
+        else if (partial) continue;
         else {
             /* a factor whose variables are all kept (never eliminated) is a
              * root item only if it has no variables at all */
@@ -679,10 +685,17 @@ static int bte_forward_k(int nvars, sliced_t *S, const int *order, int n, int op
         int p = -1;
         for (int j = 0; j < B->msg[i].nv; ++j) {
             int q = B->pos[B->msg[i].v[j]];
-            if (q < 0) return E_ARG;
+            if (q < 0) {
+                if (partial) continue;
+                return E_ARG;
+            }
             if (p < 0 || q < p) p = q;
         }
         B->parent[i] = p;
+        if (p < 0 && partial && B->msg[i].nv > 0) {
+            fac_free(&B->msg[i]);
+            continue;
+        }
         if (p >= 0) bte_add(B, p, -(i + 1));
         else if (op == OP_SUM) root += log(B->msg[i].t[0]) + B->msg[i].lsc;
         else root += B->msg[i].t[0];
@@ -778,6 +791,69 @@ int or_ve_pr(int nvars, const int *card, int nf, const int *off, const int *sv,
     double lr;
     rc = bte_forward_k(nvars, &S, order, n, OP_SUM, &B, &lr, 0);
     if (!rc) *logz = lr;
+    bte_free(&B);
+    free(order);
+    sliced_free(&S);
+    return rc;
+}
+
+/* Bounded sample of a PR elimination: eliminate only the first `nelim`
+ * variables of `order` (a full order of the unobserved variables), freeing
+ * consumed messages.  work_prefix / work_full receive the sum, over the
+ * buckets eliminated / over all buckets, of the entries a bucket visits
+ * (product of the domain sizes of its scope), counted symbolically, so that
+ * the time of the prefix scales to the time of the full elimination. */
+int or_ve_pr_prefix(int nvars, const int *card, int nf, const int *off, const int *sv,
+                    const double *tab, const int *evid, const int *order_in, int nelim,
+                    double *work_prefix, double *work_full) {
+    sliced_t S;
+    int rc = slice_all(nvars, card, nf, off, sv, tab, evid, 0, &S);
+    if (rc) return rc;
+    int *order = (int *)malloc(sizeof(int) * (size_t)(nvars + 1));
+    int n = make_order(nvars, &S, evid, order_in, order);
+    if (nelim > n) nelim = n;
+    /* symbolic work */
+    {
+        int (*scope)[4 * MAXS + 1] = malloc(sizeof(*scope) * (size_t)(S.nf + n + 1));
+        int *alive = calloc((size_t)(S.nf + n + 1), sizeof(int));
+        int cnt = 0;
+        for (int f = 0; f < S.nf; ++f) {
+            scope[cnt][0] = S.f[f].nv;
+            for (int k = 0; k < S.f[f].nv; ++k) scope[cnt][1 + k] = S.f[f].v[k];
+            alive[cnt++] = 1;
+        }
+        double wp = 0, wf = 0;
+        for (int i = 0; i < n; ++i) {
+            int v = order[i], us[4 * MAXS], nu = 0;
+            for (int f = 0; f < cnt; ++f) {
+                if (!alive[f]) continue;
+                int has = 0;
+                for (int k = 0; k < scope[f][0]; ++k) if (scope[f][1 + k] == v) has = 1;
+                if (!has) continue;
+                alive[f] = 0;
+                for (int k = 0; k < scope[f][0]; ++k) {
+                    int u = scope[f][1 + k], seen = 0;
+                    for (int j = 0; j < nu; ++j) if (us[j] == u) seen = 1;
+                    if (!seen && nu < 4 * MAXS) us[nu++] = u;
+                }
+            }
+            double w = 1;
+            for (int j = 0; j < nu; ++j) w *= card[us[j]];
+            wf += w;
+            if (i < nelim) wp += w;
+            int m = 0;
+            for (int j = 0; j < nu && m < 4 * MAXS; ++j) if (us[j] != v) scope[cnt][1 + m++] = us[j];
+            scope[cnt][0] = m;
+            alive[cnt++] = 1;
+        }
+        *work_prefix = wp;
+        *work_full = wf;
+        free(scope);
+        free(alive);
+    }
+    bte_t B;
+    double lr;
+    rc = bte_forward_k(nvars, &S, order, nelim, OP_SUM, &B, &lr, -1);
     bte_free(&B);
     free(order);
     sliced_free(&S);

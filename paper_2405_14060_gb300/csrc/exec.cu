@@ -18,8 +18,11 @@
 #include <tuple>
 #include <vector>
 
+#include "gemm.cuh"
 #include "kernels.cuh"
+#include "micro.cuh"
 #include "model.h"
+#include "stream.cuh"
 #include "task_kernels.cuh"
 #include "tn.h"
 #include "tn_internal.h"
@@ -105,6 +108,29 @@ struct DevMem {
 
 enum Kind { K_PR = 0, K_MAR = 1, K_MAP = 2, K_SAMPLE = 3, K_SUMNET = 4, K_MAXNET = 5 };
 
+// Kernel classes for profiling.
+enum Cls { C_SMALL = 0, C_STREAM = 1, C_SPLITK = 2, C_TCGEMM = 3, C_SIMTGEMM = 4, C_PREP = 5,
+           C_GENERIC = 6, C_NCLS = 8 };
+
+struct GemmOp {
+    PDesc px, py, post;
+    bool has_post = false;
+    bool direct = false;
+    bool tc = false;
+    GDesc g;
+    double prep_bytes = 0, post_bytes = 0;
+};
+
+struct Step {
+    int kind = 0;          // 0: strided contraction, 1: GEMM form, 2: absorb, 3: reduce
+    int semiring = 0;
+    CDesc d;
+    GemmOp g;
+    ADesc ad;
+    RDesc rd;
+    double flops = 0, bytes = 0;   // algorithmic: 2 * multiply-adds; operands + result once
+};
+
 struct Program {
     int kind = 0, dtype = 0, esz = 8, nbeta = 1;
     bool grads = false;
@@ -135,7 +161,15 @@ struct Program {
     double *d_logz = nullptr, *d_sigma = nullptr, *d_marg = nullptr, *d_grad = nullptr;
     int32_t *d_assign = nullptr;
     int *d_card = nullptr;
-    std::vector<CDesc> fdesc, bdesc;
+    std::vector<CDesc> fdesc;      // generic descriptor of every forward node
+    std::vector<Step> fsteps, bsteps;
+    std::vector<char> micro;                       // node runs inside a micro subtree
+    std::vector<MicroDesc> mf, mb;                 // forward / backward micro lists
+    std::vector<int32_t> mf_beg, mb_beg;           // per subtree start index
+    MicroDesc *d_mf = nullptr, *d_mb = nullptr;
+    int32_t *d_mf_beg = nullptr, *d_mb_beg = nullptr;
+    char *wsX = nullptr, *wsY = nullptr, *wsD = nullptr;
+    int gemm_type = 1;
     std::vector<LeafRec> leafrec;   // host copy (external sources patched per call)
     cudaGraphExec_t gexec = nullptr;
     int launches = 0;
@@ -154,6 +188,7 @@ struct tn_model {
     std::vector<int> slice_vars;
     double *d_tables = nullptr;
     int *d_flags = nullptr;            // [0]: tables hold logarithms
+    int *d_err = nullptr;              // set by a device-side wait that gave up
     bool tables_overridden = false;
     int device = -1;
     cudaStream_t stream = nullptr;
@@ -165,6 +200,7 @@ struct tn_model {
         progs.clear();
         if (d_tables) cudaFree(d_tables);
         if (d_flags) cudaFree(d_flags);
+        if (d_err) cudaFree(d_err);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
         if (stream) cudaStreamDestroy(stream);
@@ -293,6 +329,424 @@ std::string make_desc(const std::vector<int> &card, const Labels &la, bool ba, i
 
 int64_t elem_bytes(int dtype) { return dtype == 0 ? 8 : 4; }
 
+struct Opnd {
+    const Labels *lab;
+    bool beta;
+    int64_t per;
+    const void *ptr;
+    const unsigned long long *mx;
+};
+
+struct PDim { int64_t sz, sin, sout; bool beta; };
+
+// Fill a PDesc from logical dims (slowest first), fusing neighbours whose
+// input and output strides are both contiguous.
+static std::string fill_pdesc(std::vector<PDim> dims, PDesc &p) {
+    std::vector<PDim> f;
+    for (auto &x : dims) {
+        if (x.sz == 1 && !x.beta) continue;
+        if (!f.empty() && !f.back().beta && !x.beta && f.back().sin == x.sin * x.sz &&
+            f.back().sout == x.sout * x.sz && f.back().sz * x.sz < (1LL << 31)) {
+            f.back().sz *= x.sz;
+            f.back().sin = x.sin;
+            f.back().sout = x.sout;
+            continue;
+        }
+        f.push_back(x);
+    }
+    if ((int)f.size() > MAXD) return "permutation has too many dimensions";
+    p.nd = (int)f.size();
+    p.total = 1;
+    p.beta_dim = -1;
+    bool p2 = true;
+    for (auto &x : f) {
+        p.total *= x.sz;
+        p2 = p2 && (x.sz & (x.sz - 1)) == 0;
+    }
+    p.pow2 = p2;
+    int sh = 0;
+    for (int i = p.nd - 1; i >= 0; --i) {
+        p.sz[i] = (int32_t)f[i].sz;
+        p.sin[i] = f[i].sin;
+        p.sout[i] = f[i].sout;
+        p.sh[i] = sh;
+        if (f[i].beta) p.beta_dim = i;
+        if (p2) sh += __builtin_ctzll((unsigned long long)f[i].sz);
+    }
+    return "";
+}
+
+// One contraction in GEMM form: D[b][r][c] = sum_k X[b][r][k] Y[b][c][k] with
+// the batch label placed in the batch group if both operands carry it, else
+// in the rows (X) or columns (Y).  X and Y are prepared into workspaces in
+// the GEMM input type (per-item scaled); D goes straight into the output
+// tensor when its layout is [batch][rows][cols], else through a workspace
+// and a scatter that records the output's per-item maxima.
+static std::string make_gemm_op(const std::vector<int> &card, int nbeta, int store_t, int gemm_t,
+                                const Opnd &X, const Opnd &Y, const Labels &bt,
+                                const Labels &rows, const Labels &cols, const Labels &red,
+                                const Labels &out_lab, bool out_beta, void *out_ptr,
+                                unsigned long long *out_mx, GemmOp &op, size_t &nx, size_t &ny,
+                                size_t &nd) {
+    std::memset(&op.px, 0, sizeof op.px);
+    std::memset(&op.py, 0, sizeof op.py);
+    std::memset(&op.post, 0, sizeof op.post);
+    std::memset(&op.g, 0, sizeof op.g);
+    int bpos = X.beta && Y.beta ? 1 : X.beta ? 2 : Y.beta ? 3 : 0;
+    if (out_beta != (bpos != 0)) return "batch label placement";
+    auto prod = [&](const Labels &l) {
+        int64_t q = 1;
+        for (int v : l) q *= card[v];
+        return q;
+    };
+    const int64_t NB = nbeta;
+    int64_t B = prod(bt) * (bpos == 1 ? NB : 1);
+    int64_t R = prod(rows) * (bpos == 2 ? NB : 1);
+    int64_t C = prod(cols) * (bpos == 3 ? NB : 1);
+    int64_t K = prod(red);
+    int64_t Kld = (K + 7) & ~(int64_t)7;
+    int gsz = gemm_t == E_F64 ? 8 : gemm_t == E_F32 ? 4 : 2;
+    int ssz = store_t == E_F64 ? 8 : 4;
+    auto prep = [&](const Opnd &O, const Labels &mid, bool beta_mid, PDesc &p) -> std::string {
+        std::vector<PDim> dims;
+        auto push = [&](int64_t sz, int64_t sin, bool beta) { dims.push_back({sz, sin, 0, beta}); };
+        if (bpos == 1) push(NB, O.per, true);
+        for (int v : bt) push(card[v], stride_in(card, *O.lab, v), false);
+        if (beta_mid) push(NB, O.per, true);
+        for (int v : mid) push(card[v], stride_in(card, *O.lab, v), false);
+        size_t nred = red.size();
+        for (int v : red) push(card[v], stride_in(card, *O.lab, v), false);
+        int64_t acc = 1;
+        for (int i = (int)dims.size() - 1; i >= 0; --i) {
+            dims[i].sout = acc;
+            acc *= dims[i].sz;
+            if (i == (int)(dims.size() - nred)) acc = acc / K * Kld;   // padded K row
+        }
+        if (nred == 0) return "GEMM without a summed label";
+        std::string e = fill_pdesc(dims, p);
+        if (!e.empty()) return e;
+        if (!O.beta) p.beta_dim = -1;
+        p.mxi = O.mx;
+        p.mxi_bs = O.beta ? 1 : 0;
+        p.in_type = store_t;
+        p.out_type = gemm_t;
+        p.in = O.ptr;
+        p.out = nullptr;   // workspace, patched after allocation
+        return "";
+    };
+    std::string e = prep(X, rows, bpos == 2, op.px);
+    if (!e.empty()) return e;
+    e = prep(Y, cols, bpos == 3, op.py);
+    if (!e.empty()) return e;
+    op.prep_bytes = (double)(B * R * K + B * C * K) * (ssz + gsz);
+    GDesc &g = op.g;
+    g.R = R;
+    g.C = C;
+    g.K = K;
+    g.batch = B;
+    g.ldx = g.ldy = Kld;
+    g.bsx = R * Kld;
+    g.bsy = C * Kld;
+    g.xtype = gemm_t;
+    // canonical label sequence of D ([b][r][c]); -1 marks the batch label
+    std::vector<int> canon, target;
+    if (bpos == 1) canon.push_back(-1);
+    canon.insert(canon.end(), bt.begin(), bt.end());
+    if (bpos == 2) canon.push_back(-1);
+    canon.insert(canon.end(), rows.begin(), rows.end());
+    if (bpos == 3) canon.push_back(-1);
+    canon.insert(canon.end(), cols.begin(), cols.end());
+    if (out_beta) target.push_back(-1);
+    target.insert(target.end(), out_lab.begin(), out_lab.end());
+    op.direct = canon == target && bpos != 3;
+    g.ldd = C;
+    g.bsd = R * C;
+    if (op.direct) {
+        g.D = out_ptr;
+        g.mxd = out_mx;
+        g.beta_div_batch = bpos == 1 ? B / NB : 0;
+        g.beta_div_row = bpos == 2 ? R / NB : 0;
+        op.has_post = false;
+        nd = 0;
+    } else {
+        g.D = nullptr;     // workspace
+        g.mxd = nullptr;
+        // scatter D into the target layout
+        std::vector<int64_t> cst(canon.size());
+        int64_t acc = 1;
+        for (int i = (int)canon.size() - 1; i >= 0; --i) {
+            cst[i] = acc;
+            acc *= canon[i] < 0 ? NB : card[canon[i]];
+        }
+        auto cstride = [&](int v) {
+            for (size_t i = 0; i < canon.size(); ++i)
+                if (canon[i] == v) return cst[i];
+            return (int64_t)-1;
+        };
+        std::vector<PDim> dims;
+        for (int v : target) dims.push_back({v < 0 ? NB : card[v], cstride(v), 0, v < 0});
+        acc = 1;
+        for (int i = (int)dims.size() - 1; i >= 0; --i) {
+            dims[i].sout = acc;
+            acc *= dims[i].sz;
+        }
+        for (auto &x : dims)
+            if (x.sin < 0) return "GEMM output label missing";
+        e = fill_pdesc(dims, op.post);
+        if (!e.empty()) return e;
+        op.post.mxi = nullptr;
+        op.post.mxo = out_mx;
+        op.post.in_type = store_t;
+        op.post.out_type = store_t;
+        op.post.in = nullptr;    // workspace
+        op.post.out = out_ptr;
+        op.has_post = true;
+        op.post_bytes = (double)B * R * C * ssz * 2;
+        nd = (size_t)(B * R * C) * ssz;
+    }
+    nx = (size_t)(B * R * Kld) * gsz;
+    ny = (size_t)(B * C * Kld) * gsz;
+    return "";
+}
+
+// ----------------------------------------------------- streaming kernels
+
+struct SDim { int64_t sz, s0, s1, s2; };
+
+static std::vector<SDim> fuse3(const std::vector<SDim> &raw) {
+    std::vector<SDim> out;
+    for (auto &x : raw) {
+        if (x.sz == 1) continue;
+        if (!out.empty()) {
+            SDim &c = out.back();
+            if (c.s0 == x.s0 * x.sz && c.s1 == x.s1 * x.sz && c.s2 == x.s2 * x.sz &&
+                c.sz * x.sz < (1LL << 31)) {
+                c.sz *= x.sz;
+                c.s0 = x.s0;
+                c.s1 = x.s1;
+                c.s2 = x.s2;
+                continue;
+            }
+        }
+        out.push_back(x);
+    }
+    return out;
+}
+
+static int64_t sin_or0(const std::vector<int> &card, const Labels &l, const std::set<int> &s, int v) {
+    return s.count(v) ? stride_in(card, l, v) : 0;
+}
+
+// Flat offsets of every combination of `labs` (row-major) in two tensors.
+template <typename O>
+static bool combo_offsets(const std::vector<int> &card, const Labels &labs, const Labels &l0,
+                          const std::set<int> &s0, const Labels &l1, const std::set<int> &s1,
+                          int maxn, int &n, O *o0, O *o1) {
+    int64_t tot = 1;
+    for (int v : labs) tot *= card[v];
+    if (tot > maxn) return false;
+    n = (int)tot;
+    for (int64_t i = 0; i < tot; ++i) {
+        int64_t r = i, a = 0, b = 0;
+        for (int k = (int)labs.size() - 1; k >= 0; --k) {
+            int v = labs[k];
+            int64_t dg = r % card[v];
+            r /= card[v];
+            a += dg * sin_or0(card, l0, s0, v);
+            b += dg * sin_or0(card, l1, s1, v);
+        }
+        if ((int64_t)(O)a != a || (int64_t)(O)b != b) return false;
+        o0[i] = (O)a;
+        o1[i] = (O)b;
+    }
+    return true;
+}
+
+// Absorb: X streamed once, W small; Y's labels = R (from X) + T (new).
+static bool make_absorb(const std::vector<int> &card, const Labels &lx, bool bx, int64_t perx,
+                        const void *X, const unsigned long long *mxx, const Labels &lw, bool bw,
+                        int64_t perw, const void *W, const unsigned long long *mxw,
+                        const Labels &ly, bool by, int64_t pery, void *Y,
+                        unsigned long long *mxy, const Labels *sorder, int nbeta,
+                        int32_t *argmax, ADesc &d) {
+    std::memset(&d, 0, sizeof d);
+    if (by != (bx || bw)) return false;
+    std::set<int> sx(lx.begin(), lx.end()), sw(lw.begin(), lw.end()), sy(ly.begin(), ly.end());
+    Labels R, T, S;
+    for (int v : ly) (sx.count(v) ? R : T).push_back(v);
+    if (sorder) S = *sorder;
+    else {
+        for (int v : lx)
+            if (!sy.count(v)) S.push_back(v);
+        for (int v : lw)
+            if (!sy.count(v) && !sx.count(v)) S.push_back(v);
+    }
+    if (!combo_offsets(card, S, lx, sx, lw, sw, AMAX, d.ns, d.xoff, d.wso)) return false;
+    if (!combo_offsets(card, T, ly, sy, lw, sw, AMAX, d.nt, d.yoff, d.wto)) return false;
+    {
+        int ps = 1, pt = 1;
+        while (ps < d.ns) ps <<= 1;
+        while (pt < d.nt) pt <<= 1;
+        if (ps * pt > 256) return false;
+    }
+    std::vector<SDim> raw;
+    for (int v : R)
+        raw.push_back({card[v], stride_in(card, lx, v), stride_in(card, ly, v),
+                       sin_or0(card, lw, sw, v)});
+    auto f = fuse3(raw);
+    if ((int)f.size() > MAXD) return false;
+    d.nrd = (int)f.size();
+    d.nr = 1;
+    bool p2 = true;
+    for (auto &x : f) {
+        d.nr *= x.sz;
+        p2 = p2 && (x.sz & (x.sz - 1)) == 0;
+    }
+    d.pow2r = p2;
+    int sh = 0;
+    for (int i = d.nrd - 1; i >= 0; --i) {
+        d.rsz[i] = (int32_t)f[i].sz;
+        d.rsx[i] = f[i].s0;
+        d.rsy[i] = f[i].s1;
+        d.rsw[i] = f[i].s2;
+        d.rsh[i] = sh;
+        if (p2) sh += __builtin_ctzll((unsigned long long)f[i].sz);
+    }
+    // inner dims: the fastest dims up to >= 1024 positions, offsets in 32 bits
+    d.nin = 1;
+    d.nin_d = 0;
+    int64_t ex = 0, ey = 0, ew = 0;
+    for (int i = d.nrd - 1; i >= 0 && d.nin < 1024; --i) {
+        ex += (f[i].sz - 1) * f[i].s0;
+        ey += (f[i].sz - 1) * f[i].s1;
+        ew += (f[i].sz - 1) * f[i].s2;
+        if (ex >= (1LL << 31) || ey >= (1LL << 31) || ew >= (1LL << 31)) break;
+        d.nin *= f[i].sz;
+        d.nin_d++;
+    }
+    if (d.nin_d == 0 && d.nrd > 0) return false;
+    d.nouter = d.nr / d.nin;
+    d.nbeta = by ? nbeta : 1;
+    d.bsx = (by && bx) ? perx : 0;
+    d.bsw = (by && bw) ? perw : 0;
+    d.bsy = by ? pery : 0;
+    d.X = X;
+    d.W = W;
+    d.Y = Y;
+    d.mxx = mxx;
+    d.mxw = mxw;
+    d.mxx_bs = bx ? 1 : 0;
+    d.mxw_bs = bw ? 1 : 0;
+    d.mxy = mxy;
+    d.argmax = argmax;
+    return true;
+}
+
+// Reduce: O[g, s, t] = sum_m X[g, m, s] Z[g, m, t].
+static bool make_reduce(const std::vector<int> &card, const Labels &lx, bool bx, int64_t perx,
+                        const void *X, const unsigned long long *mxx, const Labels &lz, bool bz,
+                        int64_t perz, const void *Z, const unsigned long long *mxz,
+                        const Labels &lo, bool bo, int64_t pero, void *O,
+                        unsigned long long *mxo, int nbeta, RDesc &d) {
+    std::memset(&d, 0, sizeof d);
+    if (bo != (bx || bz)) return false;
+    std::set<int> sx(lx.begin(), lx.end()), sz(lz.begin(), lz.end()), so(lo.begin(), lo.end());
+    Labels G, S, T, M;
+    for (int v : lo) {
+        bool ix = sx.count(v), iz = sz.count(v);
+        if (ix && iz) G.push_back(v);
+        else if (ix) S.push_back(v);
+        else if (iz) T.push_back(v);
+        else return false;
+    }
+    for (int v : lx)
+        if (!so.count(v)) M.push_back(v);
+    for (int v : lz)
+        if (!so.count(v) && !sx.count(v)) M.push_back(v);
+    if (!combo_offsets(card, S, lx, sx, lo, so, AMAX, d.ns, d.xoff, d.oso)) return false;
+    if (!combo_offsets(card, T, lz, sz, lo, so, AMAX, d.nt, d.zoff, d.oto)) return false;
+    std::vector<SDim> g, m;
+    for (int v : G) g.push_back({card[v], stride_in(card, lx, v), stride_in(card, lz, v), stride_in(card, lo, v)});
+    for (int v : M) m.push_back({card[v], sin_or0(card, lx, sx, v), sin_or0(card, lz, sz, v), 0});
+    auto fg = fuse3(g), fm = fuse3(m);
+    if ((int)fg.size() > MAXD || (int)fm.size() > MAXD) return false;
+    d.ngd = (int)fg.size();
+    d.ng = 1;
+    for (int i = 0; i < d.ngd; ++i) {
+        d.gsz[i] = (int32_t)fg[i].sz;
+        d.gsx[i] = fg[i].s0;
+        d.gsz2[i] = fg[i].s1;
+        d.gso[i] = fg[i].s2;
+        d.ng *= fg[i].sz;
+    }
+    d.nmd = (int)fm.size();
+    d.nm = 1;
+    bool p2 = true;
+    for (auto &x : fm) {
+        d.nm *= x.sz;
+        p2 = p2 && (x.sz & (x.sz - 1)) == 0;
+    }
+    d.pow2m = p2;
+    int sh = 0;
+    for (int i = d.nmd - 1; i >= 0; --i) {
+        d.msz[i] = (int32_t)fm[i].sz;
+        d.msx[i] = fm[i].s0;
+        d.msz2[i] = fm[i].s1;
+        d.msh[i] = sh;
+        if (p2) sh += __builtin_ctzll((unsigned long long)fm[i].sz);
+    }
+    d.nbeta = bo ? nbeta : 1;
+    d.bsx = (bo && bx) ? perx : 0;
+    d.bsz = (bo && bz) ? perz : 0;
+    d.bso = bo ? pero : 0;
+    d.X = X;
+    d.Z = Z;
+    d.O = O;
+    d.mxx = mxx;
+    d.mxz = mxz;
+    d.mxx_bs = bx ? 1 : 0;
+    d.mxz_bs = bz ? 1 : 0;
+    d.mxo = mxo;
+    return true;
+}
+
+static bool to_micro(const CDesc &d, const char *arena, int esz, const unsigned long long *mxb,
+                     const int32_t *amb, MicroDesc &m) {
+    std::memset(&m, 0, sizeof m);
+    if (d.nout > MICRO_D || d.nk > MICRO_D || d.nbeta > MICRO_BETA) return false;
+    if (d.nout_total * d.nbeta > MICRO_MAX || d.ktotal > (1LL << 30)) return false;
+    m.nout = d.nout;
+    m.nk = d.nk;
+    m.pow2 = d.pow2;
+    m.nbeta = d.nbeta;
+    m.nout_total = (int32_t)d.nout_total;
+    m.ktotal = (int32_t)d.ktotal;
+    m.offA = ((const char *)d.A - arena) / esz;
+    m.offB = ((const char *)d.B - arena) / esz;
+    m.offC = ((const char *)d.C - arena) / esz;
+    m.bsa = (int32_t)d.bsa;
+    m.bsb = (int32_t)d.bsb;
+    for (int i = 0; i < d.nout; ++i) {
+        m.osz[i] = d.osz[i];
+        m.osh[i] = d.osh[i];
+        m.osa[i] = (int32_t)d.osa[i];
+        m.osb[i] = (int32_t)d.osb[i];
+    }
+    for (int i = 0; i < d.nk; ++i) {
+        m.ksz[i] = d.ksz[i];
+        m.ksh[i] = d.ksh[i];
+        m.ksa[i] = (int32_t)d.ksa[i];
+        m.ksb[i] = (int32_t)d.ksb[i];
+    }
+    m.mxa = d.mxa ? d.mxa - mxb : -1;
+    m.mxb = d.mxb ? d.mxb - mxb : -1;
+    m.mxc = d.mxc ? d.mxc - mxb : -1;
+    m.mxa_bs = d.mxa_bs;
+    m.mxb_bs = d.mxb_bs;
+    m.amoff = d.argmax ? d.argmax - amb : -1;
+    return true;
+}
+
 // Build (plan, allocate, describe, capture) a program.
 tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind, int dtype,
                         int nbeta, bool grads, const tn_options *opts, Program &P,
@@ -302,12 +756,15 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
     P.esz = (int)elem_bytes(dtype);
     P.nbeta = nbeta;
     P.grads = grads;
-    std::string err = build_plan(net, tree, P.plan);
+    const bool maxplus = kind == K_MAP || kind == K_MAXNET;
+    tn_prec prec = opts ? opts->prec : TN_FP64;
+    P.gemm_type = prec == TN_FP64 ? E_F64 : prec == TN_BF16 ? E_BF16 : E_F32;
+    const bool use_tc = prec == TN_TF32 || prec == TN_BF16;
+    std::string err = build_plan(net, tree, P.plan, maxplus ? 0 : 64);
     if (!err.empty()) return fail(TN_E_ORDER, err);
     const Plan &pl = P.plan;
     const int n = tree.nleaves;
     const int NN = 2 * n - 1;
-    const bool maxplus = kind == K_MAP || kind == K_MAXNET;
     const bool backward = kind == K_MAR;
     const bool keep_all = kind != K_PR && kind != K_SUMNET;
     P.fwd.assign(NN, Slot());
@@ -347,24 +804,70 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
         }
     }
     P.nmx = nmx;
-    // ---- arena offsets
+    // ---- micro subtrees: maximal subtrees of at most MICRO_NODES nodes whose
+    // tensors (and adjoints) all hold at most MICRO_MAX entries
+    P.micro.assign(NN, 0);
+    std::vector<int> micro_root(NN, -1);
+    if (nbeta <= MICRO_BETA) {
+        std::vector<char> small(NN, 0);
+        std::vector<int> cnt(NN, 0);
+        const int INF = 1 << 29;
+        auto emax = [&](int id) {
+            int64_t e = P.fwd[id].elems;
+            if (backward) e = std::max(e, P.adj[id].elems);
+            return e;
+        };
+        for (int id = n; id < NN; ++id) {
+            const Node &nd = pl.node[id];
+            bool ok = !nd.gemm && emax(id) <= MICRO_MAX && emax(nd.a) <= MICRO_MAX &&
+                      emax(nd.b) <= MICRO_MAX && (nd.a < n || small[nd.a]) &&
+                      (nd.b < n || small[nd.b]);
+            small[id] = ok;
+            cnt[id] = ok ? 1 + (nd.a < n ? 0 : cnt[nd.a]) + (nd.b < n ? 0 : cnt[nd.b]) : INF;
+        }
+        for (int id = NN - 1; id >= n; --id) {
+            int par = pl.node[id].parent;
+            if (par >= 0 && micro_root[par] >= 0) {
+                micro_root[id] = micro_root[par];
+            } else if (small[id] && cnt[id] <= MICRO_NODES) {
+                micro_root[id] = id;
+            }
+            if (micro_root[id] >= 0) P.micro[id] = 1;
+        }
+    }
+    std::map<int, std::vector<int>> msub;   // micro root -> its nodes (ascending)
+    for (int id = n; id < NN; ++id)
+        if (P.micro[id]) msub[micro_root[id]].push_back(id);
+    // ---- arena offsets, in execution order: leaves, micro subtrees, the
+    // other nodes in id order; adjoints in the backward's order
+    std::vector<int> fwd_order, bwd_order;
+    for (auto &kv : msub)
+        for (int id : kv.second) fwd_order.push_back(id);
+    for (int id = n; id < NN; ++id)
+        if (!P.micro[id]) fwd_order.push_back(id);
+    for (int id = NN - 1; id >= n; --id)
+        if (!P.micro[id]) bwd_order.push_back(id);
+    for (auto &kv : msub)
+        for (auto it = kv.second.rbegin(); it != kv.second.rend(); ++it) bwd_order.push_back(*it);
     OffsetAlloc A;
     for (int id = 0; id < n; ++id) P.fwd[id].off = A.alloc(P.fwd[id].elems);
-    for (int id = n; id < NN; ++id) {
+    // Micro subtrees run concurrently (one CTA each), so memory is never
+    // recycled inside the micro phase; their tensors are tiny.
+    for (int id : fwd_order) {
         const Node &nd = pl.node[id];
         P.fwd[id].off = A.alloc(P.fwd[id].elems);
-        if (!keep_all) {
+        if (!keep_all && !P.micro[id]) {
             A.release(P.fwd[nd.a].off, P.fwd[nd.a].elems);
             A.release(P.fwd[nd.b].off, P.fwd[nd.b].elems);
         }
     }
     if (backward) {
         P.adj[pl.root].off = A.alloc(P.adj[pl.root].elems);
-        for (int id = NN - 1; id >= n; --id) {
+        for (int id : bwd_order) {
             const Node &nd = pl.node[id];
             for (int c : {nd.a, nd.b})
                 if (P.need_adj[c]) P.adj[c].off = A.alloc(P.adj[c].elems);
-            A.release(P.adj[id].off, P.adj[id].elems);
+            if (!P.micro[id]) A.release(P.adj[id].off, P.adj[id].elems);
         }
     }
     P.arena_elems = A.top;
@@ -418,53 +921,255 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
         P.leafrec.push_back(r);
     }
     P.nleafrec = n;
-    // ---- descriptors
+    // ---- descriptors and steps
     auto mxp = [&](int64_t i) { return maxplus ? nullptr : P.mx + i; };
-    size_t scratch = 0;
+    auto fptr = [&](int id) { return (char *)P.arena + P.fwd[id].off * P.esz; };
+    auto aptr = [&](int id) { return (char *)P.arena + P.adj[id].off * P.esz; };
+    const int store_t = dtype == 0 ? E_F64 : E_F32;
+    size_t scratch = 0, need_x = 0, need_y = 0, need_d = 0;
+    auto add_gemm = [&](std::vector<Step> &steps, const Opnd &X, const Opnd &Y, const Labels &bt,
+                        const Labels &rows, const Labels &cols, const Labels &red,
+                        const Labels &out_lab, bool out_beta, void *out_ptr,
+                        unsigned long long *out_mx, double flops, double bytes) -> std::string {
+        Step st;
+        st.kind = 1;
+        size_t nx, ny, nd2;
+        std::string e = make_gemm_op(net.card, nbeta, store_t, P.gemm_type, X, Y, bt, rows, cols,
+                                     red, out_lab, out_beta, out_ptr, out_mx, st.g, nx, ny, nd2);
+        if (!e.empty()) return e;
+        st.g.tc = use_tc;
+        need_x = std::max(need_x, nx);
+        need_y = std::max(need_y, ny);
+        need_d = std::max(need_d, nd2);
+        st.flops = flops;
+        st.bytes = bytes;
+        steps.push_back(st);
+        return "";
+    };
+    auto per_items = [&](bool b) { return b ? (double)nbeta : 1.0; };
     for (int id = n; id < NN; ++id) {
         const Node &nd = pl.node[id];
         CDesc d;
         err = make_desc(net.card, pl.node[nd.a].labels, pl.node[nd.a].beta, P.fwd[nd.a].per,
-                        (char *)P.arena + P.fwd[nd.a].off * P.esz,
-                        mxp(P.fwd[nd.a].mx), pl.node[nd.b].labels, pl.node[nd.b].beta,
-                        P.fwd[nd.b].per, (char *)P.arena + P.fwd[nd.b].off * P.esz,
-                        mxp(P.fwd[nd.b].mx), nd.labels, nd.beta,
-                        (char *)P.arena + P.fwd[id].off * P.esz, mxp(P.fwd[id].mx), &nd.elim,
-                        nbeta, maxplus ? P.am + P.am_off[id] : nullptr, d);
+                        fptr(nd.a), mxp(P.fwd[nd.a].mx), pl.node[nd.b].labels, pl.node[nd.b].beta,
+                        P.fwd[nd.b].per, fptr(nd.b), mxp(P.fwd[nd.b].mx), nd.labels, nd.beta,
+                        fptr(id), mxp(P.fwd[id].mx), &nd.elim, nbeta,
+                        maxplus ? P.am + P.am_off[id] : nullptr, d);
         if (!err.empty()) return fail(TN_E_UNSUPPORTED, err);
-        scratch = std::max(scratch, contract_scratch_bytes(d, P.esz));
         P.fdesc.push_back(d);
+        if (P.micro[id]) continue;
+        double items = per_items(nd.beta);
+        double flops = 2.0 * nd.muladds * items;
+        double bytes = (double)P.esz * (P.fwd[nd.a].elems + P.fwd[nd.b].elems + P.fwd[id].elems);
+        if (nd.gemm) {
+            Opnd X{&pl.node[nd.ga].labels, pl.node[nd.ga].beta, P.fwd[nd.ga].per, fptr(nd.ga),
+                   P.mx + P.fwd[nd.ga].mx};
+            Opnd Y{&pl.node[nd.gb].labels, pl.node[nd.gb].beta, P.fwd[nd.gb].per, fptr(nd.gb),
+                   P.mx + P.fwd[nd.gb].mx};
+            err = add_gemm(P.fsteps, X, Y, nd.gbt, nd.gm, nd.gn, nd.elim, nd.labels, nd.beta,
+                           fptr(id), P.mx + P.fwd[id].mx, flops, bytes);
+            if (!err.empty()) return fail(TN_E_UNSUPPORTED, err);
+        } else {
+            Step st;
+            st.semiring = maxplus ? MAXPLUS : SUM;
+            st.flops = flops;
+            st.bytes = bytes;
+            const Node &na = pl.node[nd.a], &nb = pl.node[nd.b];
+            if (make_absorb(net.card, na.labels, na.beta, P.fwd[nd.a].per, fptr(nd.a),
+                            mxp(P.fwd[nd.a].mx), nb.labels, nb.beta, P.fwd[nd.b].per, fptr(nd.b),
+                            mxp(P.fwd[nd.b].mx), nd.labels, nd.beta, P.fwd[id].per, fptr(id),
+                            mxp(P.fwd[id].mx), &nd.elim, nbeta,
+                            maxplus ? P.am + P.am_off[id] : nullptr, st.ad) ||
+                make_absorb(net.card, nb.labels, nb.beta, P.fwd[nd.b].per, fptr(nd.b),
+                            mxp(P.fwd[nd.b].mx), na.labels, na.beta, P.fwd[nd.a].per, fptr(nd.a),
+                            mxp(P.fwd[nd.a].mx), nd.labels, nd.beta, P.fwd[id].per, fptr(id),
+                            mxp(P.fwd[id].mx), &nd.elim, nbeta,
+                            maxplus ? P.am + P.am_off[id] : nullptr, st.ad)) {
+                st.kind = 2;
+            } else if (!maxplus &&
+                       make_reduce(net.card, na.labels, na.beta, P.fwd[nd.a].per, fptr(nd.a),
+                                   mxp(P.fwd[nd.a].mx), nb.labels, nb.beta, P.fwd[nd.b].per,
+                                   fptr(nd.b), mxp(P.fwd[nd.b].mx), nd.labels, nd.beta,
+                                   P.fwd[id].per, fptr(id), mxp(P.fwd[id].mx), nbeta, st.rd) &&
+                       st.rd.nm >= 4096) {
+                st.kind = 3;
+                scratch = std::max(scratch, reduce_scratch_bytes(st.rd, P.esz));
+            } else {
+                st.kind = 0;
+                st.d = d;
+                scratch = std::max(scratch, contract_scratch_bytes(d, P.esz));
+            }
+            P.fsteps.push_back(st);
+        }
     }
     if (backward) {
         for (int id = NN - 1; id >= n; --id) {
+            if (P.micro[id]) continue;
             const Node &nd = pl.node[id];
             const Node &na = pl.node[nd.a], &nb = pl.node[nd.b];
-            char *cbar = (char *)P.arena + P.adj[id].off * P.esz;
-            CDesc d;
+            char *cbar = aptr(id);
+            double items = per_items(P.adj_beta[id]);
+            double flops = 2.0 * nd.muladds * items;
+            if (nd.gemm) {
+                const Node &xa = pl.node[nd.ga], &xb = pl.node[nd.gb];
+                Opnd Cb{&nd.labels, (bool)P.adj_beta[id], P.adj[id].per, cbar, P.mx + P.adj[id].mx};
+                Opnd A{&xa.labels, xa.beta, P.fwd[nd.ga].per, fptr(nd.ga), P.mx + P.fwd[nd.ga].mx};
+                Opnd Bo{&xb.labels, xb.beta, P.fwd[nd.gb].per, fptr(nd.gb), P.mx + P.fwd[nd.gb].mx};
+                if (P.need_adj[nd.ga]) {
+                    // Abar[bt, m, k] = sum_n Cbar[bt, m, n] B[bt, k, n]
+                    double bytes = (double)P.esz * (P.adj[id].elems + P.fwd[nd.gb].elems +
+                                                    P.adj[nd.ga].elems);
+                    err = add_gemm(P.bsteps, Cb, Bo, nd.gbt, nd.gm, nd.elim, nd.gn, xa.labels,
+                                   P.adj_beta[nd.ga], aptr(nd.ga), P.mx + P.adj[nd.ga].mx, flops,
+                                   bytes);
+                    if (!err.empty()) return fail(TN_E_UNSUPPORTED, err);
+                }
+                if (P.need_adj[nd.gb]) {
+                    // Bbar[bt, k, n] = sum_m A[bt, m, k] Cbar[bt, m, n]
+                    double bytes = (double)P.esz * (P.fwd[nd.ga].elems + P.adj[id].elems +
+                                                    P.adj[nd.gb].elems);
+                    err = add_gemm(P.bsteps, A, Cb, nd.gbt, nd.elim, nd.gn, nd.gm, xb.labels,
+                                   P.adj_beta[nd.gb], aptr(nd.gb), P.mx + P.adj[nd.gb].mx, flops,
+                                   bytes);
+                    if (!err.empty()) return fail(TN_E_UNSUPPORTED, err);
+                }
+                continue;
+            }
             if (P.need_adj[nd.a]) {
-                err = make_desc(net.card, nd.labels, P.adj_beta[id], P.adj[id].per, cbar,
+                // Abar = con(Cbar, B -> Va): stream Cbar once, B small
+                Step st;
+                st.flops = flops;
+                st.bytes = (double)P.esz * (P.adj[id].elems + P.fwd[nd.b].elems + P.adj[nd.a].elems);
+                if (make_absorb(net.card, nd.labels, P.adj_beta[id], P.adj[id].per, cbar,
                                 P.mx + P.adj[id].mx, nb.labels, nb.beta, P.fwd[nd.b].per,
-                                (char *)P.arena + P.fwd[nd.b].off * P.esz, P.mx + P.fwd[nd.b].mx,
-                                na.labels, P.adj_beta[nd.a],
-                                (char *)P.arena + P.adj[nd.a].off * P.esz, P.mx + P.adj[nd.a].mx,
-                                nullptr, nbeta, nullptr, d);
-                if (!err.empty()) return fail(TN_E_UNSUPPORTED, err);
-                scratch = std::max(scratch, contract_scratch_bytes(d, P.esz));
-                P.bdesc.push_back(d);
+                                fptr(nd.b), P.mx + P.fwd[nd.b].mx, na.labels, P.adj_beta[nd.a],
+                                P.adj[nd.a].per, aptr(nd.a), P.mx + P.adj[nd.a].mx, nullptr, nbeta,
+                                nullptr, st.ad) ||
+                    make_absorb(net.card, nb.labels, nb.beta, P.fwd[nd.b].per, fptr(nd.b),
+                                P.mx + P.fwd[nd.b].mx, nd.labels, P.adj_beta[id], P.adj[id].per,
+                                cbar, P.mx + P.adj[id].mx, na.labels, P.adj_beta[nd.a],
+                                P.adj[nd.a].per, aptr(nd.a), P.mx + P.adj[nd.a].mx, nullptr, nbeta,
+                                nullptr, st.ad)) {
+                    st.kind = 2;
+                } else {
+                    err = make_desc(net.card, nd.labels, P.adj_beta[id], P.adj[id].per, cbar,
+                                    P.mx + P.adj[id].mx, nb.labels, nb.beta, P.fwd[nd.b].per,
+                                    fptr(nd.b), P.mx + P.fwd[nd.b].mx, na.labels, P.adj_beta[nd.a],
+                                    aptr(nd.a), P.mx + P.adj[nd.a].mx, nullptr, nbeta, nullptr,
+                                    st.d);
+                    if (!err.empty()) return fail(TN_E_UNSUPPORTED, err);
+                    st.kind = 0;
+                    scratch = std::max(scratch, contract_scratch_bytes(st.d, P.esz));
+                }
+                P.bsteps.push_back(st);
             }
             if (P.need_adj[nd.b]) {
-                err = make_desc(net.card, na.labels, na.beta, P.fwd[nd.a].per,
-                                (char *)P.arena + P.fwd[nd.a].off * P.esz, P.mx + P.fwd[nd.a].mx,
-                                nd.labels, P.adj_beta[id], P.adj[id].per, cbar,
-                                P.mx + P.adj[id].mx, nb.labels, P.adj_beta[nd.b],
-                                (char *)P.arena + P.adj[nd.b].off * P.esz, P.mx + P.adj[nd.b].mx,
-                                nullptr, nbeta, nullptr, d);
-                if (!err.empty()) return fail(TN_E_UNSUPPORTED, err);
-                scratch = std::max(scratch, contract_scratch_bytes(d, P.esz));
-                P.bdesc.push_back(d);
+                // Bbar = con(A, Cbar -> Vb): stream A and Cbar once, Bbar small
+                Step st;
+                st.flops = flops;
+                st.bytes = (double)P.esz * (P.fwd[nd.a].elems + P.adj[id].elems + P.adj[nd.b].elems);
+                if (P.adj[nd.b].elems >= (1 << 16) &&
+                    (make_absorb(net.card, na.labels, na.beta, P.fwd[nd.a].per, fptr(nd.a),
+                                 P.mx + P.fwd[nd.a].mx, nd.labels, P.adj_beta[id], P.adj[id].per,
+                                 cbar, P.mx + P.adj[id].mx, nb.labels, P.adj_beta[nd.b],
+                                 P.adj[nd.b].per, aptr(nd.b), P.mx + P.adj[nd.b].mx, nullptr,
+                                 nbeta, nullptr, st.ad) ||
+                     make_absorb(net.card, nd.labels, P.adj_beta[id], P.adj[id].per, cbar,
+                                 P.mx + P.adj[id].mx, na.labels, na.beta, P.fwd[nd.a].per,
+                                 fptr(nd.a), P.mx + P.fwd[nd.a].mx, nb.labels, P.adj_beta[nd.b],
+                                 P.adj[nd.b].per, aptr(nd.b), P.mx + P.adj[nd.b].mx, nullptr,
+                                 nbeta, nullptr, st.ad))) {
+                    st.kind = 2;
+                } else if (make_reduce(net.card, na.labels, na.beta, P.fwd[nd.a].per, fptr(nd.a),
+                                P.mx + P.fwd[nd.a].mx, nd.labels, P.adj_beta[id], P.adj[id].per,
+                                cbar, P.mx + P.adj[id].mx, nb.labels, P.adj_beta[nd.b],
+                                P.adj[nd.b].per, aptr(nd.b), P.mx + P.adj[nd.b].mx, nbeta, st.rd) &&
+                    st.rd.nm >= 4096) {
+                    st.kind = 3;
+                    scratch = std::max(scratch, reduce_scratch_bytes(st.rd, P.esz));
+                } else {
+                    err = make_desc(net.card, na.labels, na.beta, P.fwd[nd.a].per, fptr(nd.a),
+                                    P.mx + P.fwd[nd.a].mx, nd.labels, P.adj_beta[id], P.adj[id].per,
+                                    cbar, P.mx + P.adj[id].mx, nb.labels, P.adj_beta[nd.b],
+                                    aptr(nd.b), P.mx + P.adj[nd.b].mx, nullptr, nbeta, nullptr,
+                                    st.d);
+                    if (!err.empty()) return fail(TN_E_UNSUPPORTED, err);
+                    st.kind = 0;
+                    scratch = std::max(scratch, contract_scratch_bytes(st.d, P.esz));
+                }
+                P.bsteps.push_back(st);
             }
         }
     }
+    // micro lists
+    for (auto &kv : msub) {
+        P.mf_beg.push_back((int32_t)P.mf.size());
+        for (int id : kv.second) {
+            MicroDesc md;
+            if (!to_micro(P.fdesc[id - n], P.arena, P.esz, P.mx, P.am, md))
+                return fail(TN_E_UNSUPPORTED, "micro node conversion");
+            P.mf.push_back(md);
+        }
+        if (!backward) continue;
+        P.mb_beg.push_back((int32_t)P.mb.size());
+        for (auto it = kv.second.rbegin(); it != kv.second.rend(); ++it) {
+            int id = *it;
+            const Node &nd = pl.node[id];
+            const Node &na = pl.node[nd.a], &nb = pl.node[nd.b];
+            char *cbar = aptr(id);
+            CDesc d;
+            MicroDesc md;
+            if (P.need_adj[nd.a]) {
+                err = make_desc(net.card, nd.labels, P.adj_beta[id], P.adj[id].per, cbar,
+                                P.mx + P.adj[id].mx, nb.labels, nb.beta, P.fwd[nd.b].per,
+                                fptr(nd.b), P.mx + P.fwd[nd.b].mx, na.labels, P.adj_beta[nd.a],
+                                aptr(nd.a), P.mx + P.adj[nd.a].mx, nullptr, nbeta, nullptr, d);
+                if (!err.empty() || !to_micro(d, P.arena, P.esz, P.mx, P.am, md))
+                    return fail(TN_E_UNSUPPORTED, "micro adjoint conversion");
+                P.mb.push_back(md);
+            }
+            if (P.need_adj[nd.b]) {
+                err = make_desc(net.card, na.labels, na.beta, P.fwd[nd.a].per, fptr(nd.a),
+                                P.mx + P.fwd[nd.a].mx, nd.labels, P.adj_beta[id], P.adj[id].per,
+                                cbar, P.mx + P.adj[id].mx, nb.labels, P.adj_beta[nd.b],
+                                aptr(nd.b), P.mx + P.adj[nd.b].mx, nullptr, nbeta, nullptr, d);
+                if (!err.empty() || !to_micro(d, P.arena, P.esz, P.mx, P.am, md))
+                    return fail(TN_E_UNSUPPORTED, "micro adjoint conversion");
+                P.mb.push_back(md);
+            }
+        }
+    }
+    P.mf_beg.push_back((int32_t)P.mf.size());
+    P.mb_beg.push_back((int32_t)P.mb.size());
+    if (!P.mf.empty()) {
+        CK(P.mem.alloc(&P.d_mf, sizeof(MicroDesc) * P.mf.size()));
+        CK(cudaMemcpy(P.d_mf, P.mf.data(), sizeof(MicroDesc) * P.mf.size(), cudaMemcpyHostToDevice));
+        CK(P.mem.alloc(&P.d_mf_beg, 4 * P.mf_beg.size()));
+        CK(cudaMemcpy(P.d_mf_beg, P.mf_beg.data(), 4 * P.mf_beg.size(), cudaMemcpyHostToDevice));
+    }
+    if (!P.mb.empty()) {
+        CK(P.mem.alloc(&P.d_mb, sizeof(MicroDesc) * P.mb.size()));
+        CK(cudaMemcpy(P.d_mb, P.mb.data(), sizeof(MicroDesc) * P.mb.size(), cudaMemcpyHostToDevice));
+        CK(P.mem.alloc(&P.d_mb_beg, 4 * P.mb_beg.size()));
+        CK(cudaMemcpy(P.d_mb_beg, P.mb_beg.data(), 4 * P.mb_beg.size(), cudaMemcpyHostToDevice));
+    }
+    // GEMM workspaces, then patch the steps' workspace pointers
+    if (need_x) CK(P.mem.alloc(&P.wsX, need_x));
+    if (need_y) CK(P.mem.alloc(&P.wsY, need_y));
+    if (need_d) CK(P.mem.alloc(&P.wsD, need_d));
+    for (auto *steps : {&P.fsteps, &P.bsteps})
+        for (auto &st : *steps) {
+            if (st.kind != 1) continue;
+            st.g.px.out = P.wsX;
+            st.g.py.out = P.wsY;
+            st.g.g.X = P.wsX;
+            st.g.g.Y = P.wsY;
+            if (st.g.has_post) {
+                st.g.g.D = P.wsD;
+                st.g.post.in = P.wsD;
+            }
+            st.g.tc = st.g.tc && tc_gemm_supported(st.g.g);
+        }
     P.scratch_bytes = scratch;
     if (scratch) CK(P.mem.alloc(&P.scratch, scratch));
     // ---- leaf records to device
@@ -596,8 +1301,74 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
     return TN_OK;
 }
 
+// Per-class device time accumulated by a profiling run.
+struct Prof {
+    double ms[C_NCLS] = {0};
+    double n[C_NCLS] = {0};
+    double flops[C_NCLS] = {0};
+    double bytes[C_NCLS] = {0};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    std::vector<double> rec;   // per launch: class, ms, flops, bytes
+};
+
+template <typename F>
+static void timed(Prof *pr, cudaStream_t st, int cls, double flops, double bytes, F &&f) {
+    if (!pr) {
+        f();
+        return;
+    }
+    cudaEventRecord(pr->e0, st);
+    f();
+    cudaEventRecord(pr->e1, st);
+    cudaEventSynchronize(pr->e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, pr->e0, pr->e1);
+    pr->ms[cls] += ms;
+    pr->n[cls] += 1;
+    pr->rec.insert(pr->rec.end(), {(double)cls, (double)ms, flops, bytes});
+    pr->flops[cls] += flops;
+    pr->bytes[cls] += bytes;
+}
+
 template <typename T>
-void enqueue_program(tn_model *m, Program &P, cudaStream_t st) {
+static void run_step(tn_model *m, Program &P, const Step &s, cudaStream_t st, int &nl, Prof *pr) {
+    if (s.kind == 2) {
+        timed(pr, st, C_STREAM, s.flops, s.bytes, [&] { launch_absorb<T>(s.ad, s.semiring, st); });
+        ++nl;
+        return;
+    }
+    if (s.kind == 3) {
+        timed(pr, st, C_SPLITK, s.flops, s.bytes, [&] { launch_reduce<T>(s.rd, P.scratch, st); });
+        nl += reduce_launches(s.rd);
+        return;
+    }
+    if (s.kind == 0) {
+        int cls = contract_uses_splitk(s.d) ? C_SPLITK : C_GENERIC;
+        timed(pr, st, cls, s.flops, s.bytes, [&] {
+            launch_contract<T>(s.d, s.semiring, P.scratch, P.scratch_bytes, st, &nl);
+        });
+        return;
+    }
+    const GemmOp &g = s.g;
+    timed(pr, st, C_PREP, 0, g.prep_bytes, [&] {
+        launch_permute(g.px, st);
+        launch_permute(g.py, st);
+    });
+    nl += 2;
+    if (g.tc) {
+        timed(pr, st, C_TCGEMM, s.flops, s.bytes, [&] { launch_tc_gemm(g.g, m->d_err, st); });
+    } else {
+        timed(pr, st, C_SIMTGEMM, s.flops, s.bytes, [&] { launch_simt_gemm(g.g, st); });
+    }
+    ++nl;
+    if (g.has_post) {
+        timed(pr, st, C_PREP, 0, g.post_bytes, [&] { launch_permute(g.post, st); });
+        ++nl;
+    }
+}
+
+template <typename T>
+void enqueue_program(tn_model *m, Program &P, cudaStream_t st, Prof *pr = nullptr) {
     const Plan &pl = P.plan;
     const int n = pl.tree.nleaves, NN = 2 * n - 1;
     const bool maxplus = P.kind == K_MAP || P.kind == K_MAXNET;
@@ -607,8 +1378,14 @@ void enqueue_program(tn_model *m, Program &P, cudaStream_t st) {
     launch_leaves<T>(P.d_leaf, P.nleafrec, m->d_tables, P.d_card, m->md.nvars, P.d_evid, P.nbeta,
                      maxplus ? 1 : 0, (T *)P.arena, P.mx, m->d_flags, st);
     ++nl;
-    for (auto &d : P.fdesc)
-        launch_contract<T>(d, maxplus ? MAXPLUS : SUM, P.scratch, P.scratch_bytes, st, &nl);
+    if (!P.mf.empty()) {
+        timed(pr, st, C_SMALL, 0, 0, [&] {
+            launch_micro<T>(P.d_mf, P.d_mf_beg, (int)P.mf_beg.size() - 1, maxplus ? MAXPLUS : SUM,
+                            (T *)P.arena, P.mx, P.am, st);
+        });
+        ++nl;
+    }
+    for (auto &s : P.fsteps) run_step<T>(m, P, s, st, nl, pr);
     const Slot &rs = P.fwd[pl.root];
     if (P.kind != K_SUMNET && P.kind != K_MAXNET) {
         launch_logz<T>(P.nbeta, (const T *)P.arena + rs.off, rs.beta ? 1 : 0, P.mx, P.d_exps,
@@ -623,7 +1400,14 @@ void enqueue_program(tn_model *m, Program &P, cudaStream_t st) {
         const Slot &ra = P.adj[pl.root];
         launch_fill_one<T>((T *)P.arena + ra.off, ra.elems, P.mx + ra.mx, st);
         ++nl;
-        for (auto &d : P.bdesc) launch_contract<T>(d, SUM, P.scratch, P.scratch_bytes, st, &nl);
+        for (auto &s : P.bsteps) run_step<T>(m, P, s, st, nl, pr);
+        if (!P.mb.empty()) {
+            timed(pr, st, C_SMALL, 0, 0, [&] {
+                launch_micro<T>(P.d_mb, P.d_mb_beg, (int)P.mb_beg.size() - 1, SUM, (T *)P.arena,
+                                P.mx, P.am, st);
+            });
+            ++nl;
+        }
         launch_marginals<T>(P.d_margrec, m->md.nvars, P.nbeta, (const T *)P.arena,
                             (const T *)P.arena, P.d_marg, P.marg_stride, st);
         ++nl;
@@ -676,6 +1460,10 @@ tn_status ensure_device(tn_model *m) {
     if (!m->d_tables) CK(cudaMalloc(&m->d_tables, tb));
     if (!m->d_flags) CK(cudaMalloc(&m->d_flags, 16));
     CK(cudaMemset(m->d_flags, 0, 16));
+    if (!m->d_err) {
+        CK(cudaMalloc(&m->d_err, 16));
+        CK(cudaMemset(m->d_err, 0, 16));
+    }
     if (!m->md.tables.empty())
         CK(cudaMemcpy(m->d_tables, m->md.tables.data(), m->md.tables.size() * 8,
                       cudaMemcpyHostToDevice));
@@ -696,7 +1484,7 @@ tn_status get_program(tn_model *m, int kind, int nbeta, const tn_options *opts, 
     }
     tn_prec prec = opts ? opts->prec : TN_FP64;
     int dtype = dtype_of(prec);
-    auto key = std::make_tuple(kind, dtype, nbeta, grads ? 1 : 0);
+    auto key = std::make_tuple(kind, (int)prec, nbeta, grads ? 1 : 0);
     auto it = m->progs.find(key);
     if (it != m->progs.end()) {
         *out = it->second.get();
@@ -724,9 +1512,20 @@ tn_status check_evid(const tn_model *m, int batch, const int32_t *evid_host) {
     return TN_OK;
 }
 
+// A bounded device-side wait that gave up leaves a flag; report and clear it.
+tn_status check_device_error(tn_model *m) {
+    int e = 0;
+    CK(cudaMemcpy(&e, m->d_err, 4, cudaMemcpyDeviceToHost));
+    if (e) {
+        CK(cudaMemset(m->d_err, 0, 4));
+        return fail(TN_E_TIMEOUT, "a device-side wait exceeded its time limit");
+    }
+    return TN_OK;
+}
+
 // Run a captured program: copy the evidence in, replay the graph, time it.
 tn_status run_program(tn_model *m, Program &P, const int32_t *evid, bool evid_on_device,
-                      cudaStream_t st) {
+                      cudaStream_t st, bool sync = true) {
     size_t eb = (size_t)P.nbeta * m->md.nvars * 4;
     if (eb) {
         if (evid)
@@ -734,6 +1533,11 @@ tn_status run_program(tn_model *m, Program &P, const int32_t *evid, bool evid_on
                                evid_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
         else
             CK(cudaMemsetAsync(P.d_evid, 0xff, eb, st));
+    }
+    if (!sync) {
+        CK(cudaGraphLaunch(P.gexec, st));
+        m->last_launches = P.launches;
+        return TN_OK;
     }
     CK(cudaEventRecord(m->ev0, st));
     CK(cudaGraphLaunch(P.gexec, st));
@@ -744,7 +1548,7 @@ tn_status run_program(tn_model *m, Program &P, const int32_t *evid, bool evid_on
     m->last_ms = ms;
     m->last_launches = P.launches;
     CK(cudaGetLastError());
-    return TN_OK;
+    return check_device_error(m);
 }
 
 cudaStream_t stream_of(tn_model *m, const tn_options *opts) {
@@ -894,11 +1698,12 @@ static tn_status pr_common(tn_model *m, int batch, const int32_t *evid, bool evi
     cudaStream_t st = stream_of(m, opts);
     s = override_tables(m, tables_dev, is_log, st);
     if (s) return s;
-    s = run_program(m, *P, evid, evid_dev, st);
+    const bool async = evid_dev && opts && opts->cuda_stream;
+    s = run_program(m, *P, evid, evid_dev, st, !async);
     if (s) return s;
     CK(cudaMemcpyAsync(logz, P->d_logz, (size_t)batch * 8,
                        logz_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    if (!async) CK(cudaStreamSynchronize(st));
     return TN_OK;
 }
 
@@ -925,12 +1730,14 @@ static tn_status mar_common(tn_model *m, int batch, const int32_t *evid, bool de
     cudaStream_t st = stream_of(m, opts);
     s = override_tables(m, tables_dev, is_log, st);
     if (s) return s;
-    s = run_program(m, *P, evid, dev, st);
+    const bool async = dev && opts && opts->cuda_stream;
+    s = run_program(m, *P, evid, dev, st, !async);
     if (s) return s;
     cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     CK(cudaMemcpyAsync(logz, P->d_logz, (size_t)batch * 8, k, st));
     CK(cudaMemcpyAsync(marg, P->d_marg, (size_t)batch * P->marg_stride * 8, k, st));
     if (grad) CK(cudaMemcpyAsync(grad, P->d_grad, (size_t)batch * P->grad_stride * 8, k, st));
+    if (async) return TN_OK;
     CK(cudaStreamSynchronize(st));
     if (!dev) {
         for (int b = 0; b < batch; ++b)
@@ -1195,7 +2002,6 @@ tn_status tn_contract_dev(int nlabels, const int *sizes, int na, const int *labe
                           const void *A, int nb, const int *labels_b, const void *B, int nc,
                           const int *labels_c, void *C, int semiring, int dtype, tn_prec prec,
                           int32_t *argmax, void *cuda_stream) {
-    (void)prec;
     if (nlabels < 0 || !sizes || (na && !labels_a) || (nb && !labels_b) || (nc && !labels_c) ||
         !A || !B || !C)
         return fail(TN_E_ARG, "NULL argument");
@@ -1222,12 +2028,80 @@ tn_status tn_contract_dev(int nlabels, const int *sizes, int na, const int *labe
         for (int v : lc)
             if (!u.count(v)) return fail(TN_E_ARG, "output label in neither operand");
     }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    // GEMM form for dense sum-product contractions (every group >= 64 entries)
+    if (semiring == 0) {
+        std::set<int> sa(la.begin(), la.end()), sb(lb.begin(), lb.end()), sc(lc.begin(), lc.end());
+        Labels bt, gm, gn, gk;
+        bool onesided = false;
+        for (int v : la) {
+            if (sc.count(v)) (sb.count(v) ? bt : gm).push_back(v);
+            else if (sb.count(v)) gk.push_back(v);
+            else onesided = true;
+        }
+        for (int v : lb)
+            if (sc.count(v) && !sa.count(v)) gn.push_back(v);
+            else if (!sc.count(v) && !sa.count(v)) onesided = true;
+        auto prod = [&](const Labels &l) {
+            int64_t q = 1;
+            for (int v : l) q *= card[v];
+            return q;
+        };
+        if (!onesided && prod(gm) >= 64 && prod(gn) >= 64 && prod(gk) >= 64) {
+            int store_t = dtype == 0 ? E_F64 : E_F32;
+            int gemm_t = dtype == 0 ? E_F64 : prec == TN_BF16 ? E_BF16 : E_F32;
+            Opnd X{&la, false, 0, A, nullptr}, Y{&lb, false, 0, B, nullptr};
+            GemmOp op;
+            size_t nx, ny, nd;
+            std::string e = make_gemm_op(card, 1, store_t, gemm_t, X, Y, bt, gm, gn, gk, lc, false,
+                                         C, nullptr, op, nx, ny, nd);
+            if (!e.empty()) return fail(TN_E_UNSUPPORTED, e);
+            void *wx = nullptr, *wy = nullptr, *wd = nullptr;
+            CK(cudaMallocAsync(&wx, nx, st));
+            CK(cudaMallocAsync(&wy, ny, st));
+            if (nd) CK(cudaMallocAsync(&wd, nd, st));
+            op.px.out = wx;
+            op.py.out = wy;
+            op.g.X = wx;
+            op.g.Y = wy;
+            if (op.has_post) {
+                op.g.D = wd;
+                op.post.in = wd;
+            }
+            bool tc = (prec == TN_TF32 || prec == TN_BF16) && dtype == 1 && tc_gemm_supported(op.g);
+            static int *d_err = nullptr;
+            if (!d_err) {
+                CK(cudaMalloc(&d_err, 16));
+                CK(cudaMemset(d_err, 0, 16));
+            }
+            launch_permute(op.px, st);
+            launch_permute(op.py, st);
+            cudaError_t le = cudaSuccess;
+            if (tc) le = launch_tc_gemm(op.g, d_err, st);
+            else launch_simt_gemm(op.g, st);
+            if (op.has_post) launch_permute(op.post, st);
+            cudaError_t e2 = cudaGetLastError();
+            cudaFreeAsync(wx, st);
+            cudaFreeAsync(wy, st);
+            if (wd) cudaFreeAsync(wd, st);
+            if (le != cudaSuccess || e2 != cudaSuccess)
+                return fail(TN_E_CUDA, std::string("GEMM launch: ") +
+                                           cudaGetErrorString(le != cudaSuccess ? le : e2));
+            CK(cudaStreamSynchronize(st));
+            int herr = 0;
+            CK(cudaMemcpy(&herr, d_err, 4, cudaMemcpyDeviceToHost));
+            if (herr) {
+                CK(cudaMemset(d_err, 0, 4));
+                return fail(TN_E_TIMEOUT, "a device-side wait exceeded its time limit");
+            }
+            return TN_OK;
+        }
+    }
     CDesc d;
     std::string err = make_desc(card, la, false, 0, A, nullptr, lb, false, 0, B, nullptr, lc,
                                 false, C, nullptr, nullptr, 1,
                                 semiring == 1 ? argmax : nullptr, d);
     if (!err.empty()) return fail(TN_E_UNSUPPORTED, err);
-    cudaStream_t st = (cudaStream_t)cuda_stream;
     int es = dtype == 0 ? 8 : 4;
     size_t sb = contract_scratch_bytes(d, es);
     void *scratch = nullptr;
@@ -1239,6 +2113,68 @@ tn_status tn_contract_dev(int nlabels, const int *sizes, int na, const int *labe
     if (e != cudaSuccess) return fail(TN_E_CUDA, std::string("contract launch: ") + cudaGetErrorString(e));
     CK(cudaStreamSynchronize(st));
     return TN_OK;
+}
+
+// Time every kernel of a PR (task 0) or PR + MAR (task 1) pass one launch at a
+// time, accumulated by kernel class over `reps` passes.  out[8][4]: per class
+// total milliseconds, launches, algorithmic FLOPs, algorithmic bytes.
+static tn_status profile_impl(tn_model *m, int task, int batch, const int32_t *evid,
+                              const tn_options *opts, int reps, double *out, int cap,
+                              double *steps, int *nsteps);
+
+tn_status tn_profile(tn_model *m, int task, int batch, const int32_t *evid,
+                     const tn_options *opts, int reps, double *out) {
+    return profile_impl(m, task, batch, evid, opts, reps, out, 0, nullptr, nullptr);
+}
+
+tn_status tn_profile_steps(tn_model *m, int task, int batch, const int32_t *evid,
+                           const tn_options *opts, int cap, double *steps, int *nsteps) {
+    double cls[32];
+    return profile_impl(m, task, batch, evid, opts, 1, cls, cap, steps, nsteps);
+}
+
+static tn_status profile_impl(tn_model *m, int task, int batch, const int32_t *evid,
+                              const tn_options *opts, int reps, double *out, int cap,
+                              double *steps, int *nsteps) {
+    if (!m || !out || batch < 1 || reps < 1 || (task != 0 && task != 1))
+        return fail(TN_E_ARG, "bad argument");
+    tn_status s = check_evid(m, batch, evid);
+    if (s) return s;
+    Program *P;
+    s = get_program(m, task == 0 ? K_PR : K_MAR, batch, opts, false, &P);
+    if (s) return s;
+    cudaStream_t st = m->stream;
+    s = override_tables(m, nullptr, 0, st);
+    if (s) return s;
+    size_t eb = (size_t)batch * m->md.nvars * 4;
+    if (eb) {
+        if (evid) CK(cudaMemcpy(P->d_evid, evid, eb, cudaMemcpyHostToDevice));
+        else CK(cudaMemset(P->d_evid, 0xff, eb));
+    }
+    Prof pr;
+    CK(cudaEventCreate(&pr.e0));
+    CK(cudaEventCreate(&pr.e1));
+    for (int r = 0; r < reps; ++r) {
+        if (P->dtype == 0) enqueue_program<double>(m, *P, st, &pr);
+        else enqueue_program<float>(m, *P, st, &pr);
+    }
+    CK(cudaStreamSynchronize(st));
+    cudaEventDestroy(pr.e0);
+    cudaEventDestroy(pr.e1);
+    if (steps && nsteps) {
+        int n = (int)(pr.rec.size() / 4);
+        *nsteps = n;
+        for (int i = 0; i < std::min(n, cap); ++i)
+            for (int j = 0; j < 4; ++j) steps[4 * i + j] = pr.rec[4 * i + j];
+    }
+    for (int c = 0; c < C_NCLS; ++c) {
+        out[4 * c + 0] = pr.ms[c] / reps;
+        out[4 * c + 1] = pr.n[c] / reps;
+        out[4 * c + 2] = pr.flops[c] / reps;
+        out[4 * c + 3] = pr.bytes[c] / reps;
+    }
+    CK(cudaGetLastError());
+    return check_device_error(m);
 }
 
 double tn_last_device_ms(const tn_model *m) { return m ? m->last_ms : 0.0; }

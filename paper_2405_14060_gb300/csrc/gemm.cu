@@ -1,0 +1,481 @@
+// Dense pairwise contractions as batched GEMMs (the paper's "each pairwise
+// contraction can be decomposed into BLAS operations", Sec. Tensor networks),
+// written for sm_103a:
+//
+//   k_permute    operand preparation: a strided tensor to GEMM form
+//                [batch][rows][K] (K contiguous), with the per-item exact
+//                power-of-two rescale and the conversion to the GEMM input
+//                type; also used to scatter a GEMM result into a tensor's
+//                layout while recording its per-item maximum.
+//   k_tc_gemm    tcgen05 tensor-core GEMM: D = X Y^T per batch, X and Y
+//                K-major, TF32 (kind::tf32) or BF16 (kind::f16) inputs staged
+//                by TMA (128-byte swizzle) through a 4-stage mbarrier
+//                pipeline, FP32 accumulator in TMEM (128 x 256 per CTA),
+//                epilogue through tcgen05.ld.  One thread issues TMA, one
+//                issues MMAs, four warps drain TMEM.
+//   k_simt_gemm  CUDA-core tiled GEMM for FP32 and FP64.
+//
+// Every mbarrier wait is bounded in time: a wait that exceeds ~2 s sets the
+// error flag and the CTA skips the rest of its work, frees its TMEM and exits.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstdio>
+#include <mutex>
+
+#include "devutil.cuh"
+#include "gemm.cuh"
+
+namespace tn {
+
+// ------------------------------------------------------------- permute
+
+template <typename T> __device__ __forceinline__ double ld_as_double(const void *p, int64_t i);
+template <> __device__ __forceinline__ double ld_as_double<float>(const void *p, int64_t i) {
+    return (double)((const float *)p)[i];
+}
+template <> __device__ __forceinline__ double ld_as_double<double>(const void *p, int64_t i) {
+    return ((const double *)p)[i];
+}
+
+template <typename TI, int OT>
+__global__ void __launch_bounds__(256) k_permute(const __grid_constant__ PDesc p, int64_t per) {
+    // blockIdx.y = batch item when the outermost dimension is the batch label
+    // and maxima are recorded (per = entries per item); else blockIdx.y = 0
+    // and per = total.
+    const int64_t item = blockIdx.y;
+    double mxv = 0;
+    constexpr int U = 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < per; i0 += stride * U) {
+        int64_t oi[U], oo[U], beta[U];
+        double v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            int64_t i = i0 + u * stride;
+            const int64_t idx = item * per + (i < per ? i : 0);
+            oi[u] = 0;
+            oo[u] = 0;
+            beta[u] = 0;
+            if (p.pow2) {
+                for (int d = 0; d < p.nd; ++d) {
+                    int64_t dg = (idx >> p.sh[d]) & (int64_t)(p.sz[d] - 1);
+                    oi[u] += dg * p.sin[d];
+                    oo[u] += dg * p.sout[d];
+                    if (d == p.beta_dim) beta[u] = dg;
+                }
+            } else {
+                int64_t r = idx;
+                for (int d = p.nd - 1; d >= 0; --d) {
+                    int64_t dg = r % p.sz[d];
+                    r /= p.sz[d];
+                    oi[u] += dg * p.sin[d];
+                    oo[u] += dg * p.sout[d];
+                    if (d == p.beta_dim) beta[u] = dg;
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = ld_as_double<TI>(p.in, oi[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (i0 + u * stride >= per) continue;
+            double x = v[u];
+            if (p.mxi) x *= pow2neg<double>(exp_of_bits(p.mxi[beta[u] * p.mxi_bs]));
+            if (OT == E_F64) ((double *)p.out)[oo[u]] = x;
+            else if (OT == E_F32) ((float *)p.out)[oo[u]] = (float)x;
+            else ((__nv_bfloat16 *)p.out)[oo[u]] = __float2bfloat16_rn((float)x);
+            mxv = fmax(mxv, x);
+        }
+    }
+    if (p.mxo) block_max_atomic(p.mxo + item, mxv);
+}
+
+void launch_permute(const PDesc &p, cudaStream_t st) {
+    if (p.total <= 0) return;
+    int nitems = 1;
+    if (p.mxo && p.beta_dim == 0) nitems = p.sz[0];
+    int64_t per = p.total / nitems;
+    dim3 grid = item_grid((per + 3) / 4, nitems);
+    if (p.in_type == E_F64) k_permute<double, E_F64><<<grid, 256, 0, st>>>(p, per);
+    else if (p.out_type == E_F32) k_permute<float, E_F32><<<grid, 256, 0, st>>>(p, per);
+    else k_permute<float, E_BF16><<<grid, 256, 0, st>>>(p, per);
+}
+
+// ------------------------------------------------------------ tcgen05 GEMM
+
+constexpr int TC_BM = 128, TC_BN = 256, TC_STAGES = 4;
+constexpr int TC_XBYTES = TC_BM * 128, TC_YBYTES = TC_BN * 128;    // one 128-byte K slab
+constexpr int TC_SMEM = TC_STAGES * (TC_XBYTES + TC_YBYTES) + 1024 + 256;
+constexpr unsigned long long TC_WAIT_NS = 2000000000ull;
+
+struct TCParams {
+    int64_t R, C, ldd, bsd;
+    int kt;                     // number of 128-byte K slabs
+    float *D;
+    unsigned long long *mxd;
+    int64_t beta_div_batch, beta_div_row;
+    int *err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: false (and the error flag set) after ~2 s
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err) {
+    if (mbar_try(bar, parity)) return true;
+    unsigned long long t0 = gtimer();
+    while (!mbar_try(bar, parity)) {
+        if (*(volatile int *)err) return false;
+        if (gtimer() - t0 > TC_WAIT_NS) {
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+    return true;
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row groups 1024 bytes apart (stride byte offset), version 1.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;                 // leading byte offset (unused for SW128 K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+    d |= (uint64_t)1 << 46;                 // descriptor version
+    d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+    return d;
+}
+
+template <int BF16>
+__global__ void __launch_bounds__(128, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUtensorMap ty,
+              const __grid_constant__ TCParams p) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *sX = smem;
+    uint8_t *sY = smem + TC_STAGES * TC_XBYTES;
+    uint64_t *bars = (uint64_t *)(sY + TC_STAGES * TC_YBYTES);
+    uint32_t *tslot = (uint32_t *)(bars + 2 * TC_STAGES + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t n0 = (int64_t)blockIdx.x * TC_BN, m0 = (int64_t)blockIdx.y * TC_BM;
+    const int bz = blockIdx.z;
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + TC_STAGES),
+                   tfull = smem_u32(bars + 2 * TC_STAGES);
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TC_STAGES; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0 + 8 * s));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty0 + 8 * s));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tfull));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&tx) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(&ty) : "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tslot)),
+                     "r"(TC_BN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    const int KT = p.kt;
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        for (int kt = 0; kt < KT; ++kt) {
+            int s = kt % TC_STAGES, round = kt / TC_STAGES;
+            if (kt >= TC_STAGES && !mbar_wait(empty0 + 8 * s, (round - 1) & 1, p.err)) break;
+            uint32_t fb = full0 + 8 * s;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                         "r"(TC_XBYTES + TC_YBYTES)
+                         : "memory");
+            int kx = kt * (BF16 ? 64 : 32);
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(sX + s * TC_XBYTES)),
+                "l"(&tx), "r"(fb), "r"(kx), "r"((int)m0), "r"(bz)
+                : "memory");
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(sY + s * TC_YBYTES)),
+                "l"(&ty), "r"(fb), "r"(kx), "r"((int)n0), "r"(bz)
+                : "memory");
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer: D[128 x 256] (+)= X[128 x K] * Y[256 x K]^T, 4 MMAs of 32 bytes of K per slab
+        const uint32_t idesc = (1u << 4) |                               // D: F32
+                               ((BF16 ? 1u : 2u) << 7) |                 // A: BF16 / TF32
+                               ((BF16 ? 1u : 2u) << 10) |                // B: BF16 / TF32
+                               ((uint32_t)(TC_BN >> 3) << 17) |          // N
+                               ((uint32_t)(TC_BM >> 4) << 24);           // M
+        bool ok = true;
+        for (int kt = 0; kt < KT; ++kt) {
+            int s = kt % TC_STAGES, round = kt / TC_STAGES;
+            if (!mbar_wait(full0 + 8 * s, round & 1, p.err)) { ok = false; break; }
+            tc_fence_after();
+            uint64_t ad = sdesc_sw128(smem_u32(sX + s * TC_XBYTES));
+            uint64_t bd = sdesc_sw128(smem_u32(sY + s * TC_YBYTES));
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                uint32_t acc = (kt | kk) ? 1u : 0u;
+                if (BF16)
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(ad + 2 * kk), "l"(bd + 2 * kk), "r"(idesc), "r"(acc));
+                else
+                    asm volatile(
+                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                        "l"(ad + 2 * kk), "l"(bd + 2 * kk), "r"(idesc), "r"(acc));
+            }
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    empty0 + 8 * s)
+                : "memory");
+        }
+        if (ok)
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    tfull)
+                : "memory");
+    }
+    __syncwarp();
+    // epilogue: warp w drains TMEM lanes 32w..32w+31 (rows of the tile)
+    bool have = mbar_wait(tfull, 0, p.err);
+    have = __all_sync(0xffffffffu, have);
+    tc_fence_after();
+    const int64_t row = m0 + warp * 32 + lane;
+    double mx = 0;
+    if (have) {
+        float *drow = p.D + (int64_t)bz * p.bsd + row * p.ldd;
+        for (int ch = 0; ch < TC_BN / 32; ++ch) {
+            uint32_t r[32];
+            uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 32);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+                "%10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, "
+                "%26, %27, %28, %29, %30, %31}, [%32];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                  "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                  "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
+                  "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                  "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+                  "=r"(r[30]), "=r"(r[31])
+                : "r"(ta));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            int64_t c0 = n0 + ch * 32;
+            if (row < p.R && c0 < p.C) {
+                if (c0 + 32 <= p.C && (p.ldd % 4) == 0) {
+                    float4 *dst = (float4 *)(drow + c0);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        float4 v;
+                        v.x = __uint_as_float(r[4 * q + 0]);
+                        v.y = __uint_as_float(r[4 * q + 1]);
+                        v.z = __uint_as_float(r[4 * q + 2]);
+                        v.w = __uint_as_float(r[4 * q + 3]);
+                        dst[q] = v;
+                        mx = fmax(mx, (double)fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
+                    }
+                } else {
+                    for (int q = 0; q < 32 && c0 + q < p.C; ++q) {
+                        float v = __uint_as_float(r[q]);
+                        drow[c0 + q] = v;
+                        mx = fmax(mx, (double)v);
+                    }
+                }
+            }
+        }
+    }
+    int64_t beta = p.beta_div_batch > 0 ? (int64_t)bz / p.beta_div_batch
+                   : p.beta_div_row > 0 ? (row < p.R ? row : p.R - 1) / p.beta_div_row
+                                        : 0;
+    record_max(p.mxd, beta, have && row < p.R, mx);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 2)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TC_BN));
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    });
+    return fn;
+}
+
+bool tc_gemm_supported(const GDesc &g) {
+    int es = g.xtype == E_BF16 ? 2 : 4;
+    if (g.xtype == E_F64) return false;
+    if (((uintptr_t)g.X | (uintptr_t)g.Y) & 15) return false;
+    if ((g.ldx * es) % 16 || (g.ldy * es) % 16) return false;
+    if (g.batch > 1 && ((g.bsx * es) % 16 || (g.bsy * es) % 16)) return false;
+    if (g.R > (1LL << 31) - TC_BM || g.C > (1LL << 31) - TC_BN || g.batch > 65535) return false;
+    if (g.K < 1) return false;
+    return encode_fn() != nullptr;
+}
+
+static bool make_map(CUtensorMap *m, const void *base, int64_t K, int64_t rows, int64_t batch,
+                     int64_t ld, int64_t bs, int es, bool bf16, int box_rows) {
+    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)batch};
+    cuuint64_t strides[2] = {(cuuint64_t)(ld * es), (cuuint64_t)((batch > 1 ? bs : rows * ld) * es)};
+    cuuint32_t box[3] = {(cuuint32_t)(128 / es), (cuuint32_t)box_rows, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode_fn()(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                             3, (void *)base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+cudaError_t launch_tc_gemm(const GDesc &g, int *err_flag, cudaStream_t st) {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(k_tc_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+        cudaFuncSetAttribute(k_tc_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    });
+    bool bf16 = g.xtype == E_BF16;
+    int es = bf16 ? 2 : 4;
+    CUtensorMap mx, my;
+    if (!make_map(&mx, g.X, g.K, g.R, g.batch, g.ldx, g.bsx, es, bf16, TC_BM) ||
+        !make_map(&my, g.Y, g.K, g.C, g.batch, g.ldy, g.bsy, es, bf16, TC_BN))
+        return cudaErrorInvalidValue;
+    TCParams p;
+    p.R = g.R;
+    p.C = g.C;
+    p.ldd = g.ldd;
+    p.bsd = g.bsd;
+    int kel = 128 / es;
+    p.kt = (int)((g.K + kel - 1) / kel);
+    p.D = (float *)g.D;
+    p.mxd = g.mxd;
+    p.beta_div_batch = g.beta_div_batch;
+    p.beta_div_row = g.beta_div_row;
+    p.err = err_flag;
+    dim3 grid((unsigned)((g.C + TC_BN - 1) / TC_BN), (unsigned)((g.R + TC_BM - 1) / TC_BM),
+              (unsigned)g.batch);
+    if (bf16) k_tc_gemm<1><<<grid, 128, TC_SMEM, st>>>(mx, my, p);
+    else k_tc_gemm<0><<<grid, 128, TC_SMEM, st>>>(mx, my, p);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- SIMT GEMM
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_simt_gemm(const __grid_constant__ GDesc g) {
+    constexpr int BM = 64, BN = 64, BK = 16;
+    __shared__ T sx[BK][BM + 1];
+    __shared__ T sy[BK][BN + 1];
+    const int t = threadIdx.x, ty = t / 16, tx = t % 16;
+    const int64_t r0 = (int64_t)blockIdx.y * BM, c0 = (int64_t)blockIdx.x * BN;
+    const int64_t b = blockIdx.z;
+    const T *X = (const T *)g.X + b * g.bsx;
+    const T *Y = (const T *)g.Y + b * g.bsy;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+    for (int64_t k0 = 0; k0 < g.K; k0 += BK) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int e = t + i * 256, rr = e / BK, kk = e % BK;
+            int64_t gr = r0 + rr, gc = c0 + rr, gk = k0 + kk;
+            sx[kk][rr] = (gr < g.R && gk < g.K) ? X[gr * g.ldx + gk] : T(0);
+            sy[kk][rr] = (gc < g.C && gk < g.K) ? Y[gc * g.ldy + gk] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            T a[4], c[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = sx[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) c[j] = sy[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * c[j];
+        }
+        __syncthreads();
+    }
+    double mx = 0;
+    T *D = (T *)g.D + b * g.bsd;
+    int64_t rowlast = r0 + ty * 4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int64_t r = r0 + ty * 4 + i;
+        if (r >= g.R) continue;
+        rowlast = r;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int64_t c = c0 + tx * 4 + j;
+            if (c < g.C) {
+                D[r * g.ldd + c] = acc[i][j];
+                mx = fmax(mx, (double)acc[i][j]);
+            }
+        }
+    }
+    bool any = r0 + ty * 4 < g.R;
+    int64_t beta = g.beta_div_batch > 0 ? b / g.beta_div_batch
+                   : g.beta_div_row > 0 ? (any ? rowlast : g.R - 1) / g.beta_div_row
+                                        : 0;
+    // rows ty*4..ty*4+3 of one thread may straddle items only if an item has
+    // fewer than 4 rows; record per row in that case
+    if (g.beta_div_row > 0 && g.beta_div_row < 4 && g.beta_div_batch <= 0) {
+        for (int i = 0; i < 4; ++i) {
+            int64_t r = r0 + ty * 4 + i;
+            double m1 = 0;
+            for (int j = 0; j < 4; ++j) {
+                int64_t c = c0 + tx * 4 + j;
+                if (r < g.R && c < g.C) m1 = fmax(m1, (double)acc[i][j]);
+            }
+            if (g.mxd && r < g.R && m1 > 0) atomicMax(g.mxd + r / g.beta_div_row, dbits(m1));
+        }
+        return;
+    }
+    record_max(g.mxd, beta, any, mx);
+}
+
+void launch_simt_gemm(const GDesc &g, cudaStream_t st) {
+    dim3 grid((unsigned)((g.C + 63) / 64), (unsigned)((g.R + 63) / 64), (unsigned)g.batch);
+    if (g.xtype == E_F64) k_simt_gemm<double><<<grid, 256, 0, st>>>(g);
+    else k_simt_gemm<float><<<grid, 256, 0, st>>>(g);
+}
+
+}  // namespace tn

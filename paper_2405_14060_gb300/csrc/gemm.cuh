@@ -1,0 +1,54 @@
+// Dense pairwise contractions as batched GEMMs: operand preparation
+// (permute into GEMM form, per-item power-of-two scaling, dtype conversion),
+// tcgen05 tensor-core GEMM (TF32 / BF16 in, FP32 accumulate in TMEM) and a
+// CUDA-core tiled GEMM (FP32 / FP64).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+
+namespace tn {
+
+enum ElemType { E_F64 = 0, E_F32 = 1, E_BF16 = 2 };
+
+// Permute a strided tensor into a dense layout (optionally with padded
+// innermost stride), scaling each batch item by 2^-e(max) and converting.
+//   logical dims (slowest first): sz[d]; input stride sin[d]; output stride sout[d]
+//   beta_dim: the dimension that indexes batch items for the scale (-1: none)
+//   mxo (optional): record the per-item maximum of the output (beta from beta_dim)
+struct PDesc {
+    int nd;
+    int pow2;
+    int beta_dim;
+    int in_type, out_type;      // ElemType
+    int64_t total;
+    int32_t sz[MAXD], sh[MAXD];
+    int64_t sin[MAXD], sout[MAXD];
+    const void *in;
+    void *out;
+    const unsigned long long *mxi;   // scale source (NULL: no scaling)
+    int mxi_bs;                      // 1: per item
+    unsigned long long *mxo;
+};
+
+// D[b][r][c] = sum_k X[b][r][k] * Y[b][c][k]   (X, Y K-major, D row-major FP32/FP64)
+struct GDesc {
+    int64_t R, C, K, batch;
+    int64_t ldx, ldy, ldd;          // elements
+    int64_t bsx, bsy, bsd;          // elements
+    int xtype;                      // ElemType of X and Y
+    const void *X, *Y;
+    void *D;
+    unsigned long long *mxd;        // per-item max of D (NULL: none)
+    int64_t beta_div_batch;         // item = b / beta_div_batch (if > 0)
+    int64_t beta_div_row;           // else item = r / beta_div_row (if > 0), else 0
+};
+
+void launch_permute(const PDesc &p, cudaStream_t st);
+// Returns false if the tensor-core path cannot take this problem.
+bool tc_gemm_supported(const GDesc &g);
+cudaError_t launch_tc_gemm(const GDesc &g, int *err_flag, cudaStream_t st);
+void launch_simt_gemm(const GDesc &g, cudaStream_t st);
+
+}  // namespace tn

@@ -21,28 +21,10 @@
 #include <cfloat>
 #include <cmath>
 
+#include "devutil.cuh"
 #include "kernels.cuh"
 
 namespace tn {
-
-__device__ __forceinline__ int exp_of_bits(unsigned long long b) {
-    if (b == 0ull) return 0;
-    return (int)((b >> 52) & 0x7ffull) - 1023;
-}
-
-template <typename T> __device__ __forceinline__ T pow2neg(int e);
-template <> __device__ __forceinline__ float pow2neg<float>(int e) {
-    e = max(-126, min(126, e));
-    return __int_as_float((127 - e) << 23);
-}
-template <> __device__ __forceinline__ double pow2neg<double>(int e) {
-    e = max(-1022, min(1022, e));
-    return __longlong_as_double((long long)(1023 - e) << 52);
-}
-
-__device__ __forceinline__ unsigned long long dbits(double x) {
-    return (unsigned long long)__double_as_longlong(x);
-}
 
 // offsets of output entry o in A and B
 __device__ __forceinline__ void decode_out(const CDesc &d, int64_t o, int64_t &oa, int64_t &ob) {
@@ -83,43 +65,23 @@ __device__ __forceinline__ void decode_k(const CDesc &d, int64_t k, int64_t &ka,
     }
 }
 
-// Record per-item maxima of non-negative values: one atomic per warp when the
-// warp's lanes share an item, else one per lane.
-__device__ __forceinline__ void record_max(unsigned long long *mx, int64_t beta, bool active,
-                                           double v) {
-    if (!mx) return;
-    unsigned long long m = active ? dbits(v) : 0ull;
-    long long b0 = __shfl_sync(0xffffffffu, (long long)beta, 0);
-    bool same = __all_sync(0xffffffffu, !active || beta == b0);
-    if (same) {
-#pragma unroll
-        for (int s = 16; s > 0; s >>= 1) {
-            unsigned long long o = __shfl_xor_sync(0xffffffffu, m, s);
-            m = o > m ? o : m;
-        }
-        if ((threadIdx.x & 31) == 0 && m) atomicMax(mx + b0, m);
-    } else if (active && m) {
-        atomicMax(mx + beta, m);
-    }
-}
-
 template <typename T, int SEMI>
 __global__ void __launch_bounds__(256) k_contract(const __grid_constant__ CDesc d) {
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t total = d.nout_total * d.nbeta;
-    bool active = idx < total;
-    int64_t beta = 0, o = 0;
-    T val = SEMI == SUM ? T(0) : -INFINITY;
-    if (active) {
-        beta = idx / d.nout_total;
-        o = idx - beta * d.nout_total;
+    const int64_t beta = blockIdx.y;
+    double mx = 0;
+    T sa = T(1), sb = T(1);
+    if (SEMI == SUM) {
+        sa = d.mxa ? pow2neg<T>(exp_of_bits(d.mxa[beta * d.mxa_bs])) : T(1);
+        sb = d.mxb ? pow2neg<T>(exp_of_bits(d.mxb[beta * d.mxb_bs])) : T(1);
+    }
+    for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < d.nout_total;
+         o += (int64_t)gridDim.x * blockDim.x) {
         int64_t oa = beta * d.bsa, ob = beta * d.bsb;
         decode_out(d, o, oa, ob);
         const T *A = (const T *)d.A + oa;
         const T *B = (const T *)d.B + ob;
+        const int64_t idx = beta * d.nout_total + o;
         if (SEMI == SUM) {
-            T sa = d.mxa ? pow2neg<T>(exp_of_bits(d.mxa[beta * d.mxa_bs])) : T(1);
-            T sb = d.mxb ? pow2neg<T>(exp_of_bits(d.mxb[beta * d.mxb_bs])) : T(1);
             T acc = 0;
             if (d.nk == 0) {
                 acc = (A[0] * sa) * (B[0] * sb);
@@ -134,7 +96,8 @@ __global__ void __launch_bounds__(256) k_contract(const __grid_constant__ CDesc 
                     acc += (A[ka] * sa) * (B[kb] * sb);
                 }
             }
-            val = acc;
+            ((T *)d.C)[idx] = acc;
+            mx = fmax(mx, (double)acc);
         } else {
             T best = -INFINITY;
             int32_t bk = 0;
@@ -143,23 +106,22 @@ __global__ void __launch_bounds__(256) k_contract(const __grid_constant__ CDesc 
             } else if (d.nk == 1) {
                 int64_t sA = d.ksa[0], sB = d.ksb[0];
                 for (int64_t k = 0; k < d.ktotal; ++k) {
-                    T s = A[k * sA] + B[k * sB];
-                    if (s > best) { best = s; bk = (int32_t)k; }
+                    T v = A[k * sA] + B[k * sB];
+                    if (v > best) { best = v; bk = (int32_t)k; }
                 }
             } else {
                 for (int64_t k = 0; k < d.ktotal; ++k) {
                     int64_t ka, kb;
                     decode_k(d, k, ka, kb);
-                    T s = A[ka] + B[kb];
-                    if (s > best) { best = s; bk = (int32_t)k; }
+                    T v = A[ka] + B[kb];
+                    if (v > best) { best = v; bk = (int32_t)k; }
                 }
             }
-            val = best;
+            ((T *)d.C)[idx] = best;
             if (d.argmax) d.argmax[idx] = bk;
         }
-        ((T *)d.C)[idx] = val;
     }
-    if (SEMI == SUM) record_max(d.mxc, beta, active, (double)val);
+    if (SEMI == SUM && d.mxc) block_max_atomic(d.mxc + beta, mx);
 }
 
 // ---------------------------------------------------------------- split-K
@@ -276,10 +238,14 @@ static void splitk_shape(const CDesc &d, int64_t &chunk, int &nchunks) {
     nchunks = (int)((d.ktotal + chunk - 1) / chunk);
 }
 
+// Split the summed space over blocks when the outputs alone cannot fill the
+// GPU and each output sums enough terms to make the serial loop the bottleneck.
 static bool use_splitk(const CDesc &d) {
     int64_t outs = d.nout_total * d.nbeta;
-    return d.ktotal >= 4096 && outs * 16 < kTargetThreads && outs <= (1LL << 22);
+    return d.ktotal >= 256 && outs * 64 < kTargetThreads * 4 && outs <= (1LL << 20);
 }
+
+bool contract_uses_splitk(const CDesc &d) { return use_splitk(d); }
 
 size_t contract_scratch_bytes(const CDesc &d, int elem_bytes) {
     if (!use_splitk(d)) return 0;
@@ -319,11 +285,11 @@ void launch_contract(const CDesc &d, int semiring, void *scratch, size_t scratch
         if (nlaunch) *nlaunch += 2;
         return;
     }
-    unsigned blocks = (unsigned)((total + 255) / 256);
+    dim3 grid = item_grid(d.nout_total, d.nbeta);
     if (semiring == SUM)
-        k_contract<T, SUM><<<blocks, 256, 0, st>>>(d);
+        k_contract<T, SUM><<<grid, 256, 0, st>>>(d);
     else
-        k_contract<T, MAXPLUS><<<blocks, 256, 0, st>>>(d);
+        k_contract<T, MAXPLUS><<<grid, 256, 0, st>>>(d);
     if (nlaunch) *nlaunch += 1;
 }
 

@@ -41,5 +41,6 @@ template <typename T>
 void launch_contract(const CDesc &d, int semiring, void *scratch, size_t scratch_bytes,
                      cudaStream_t st, int *nlaunch);
 size_t contract_scratch_bytes(const CDesc &d, int elem_bytes);
+bool contract_uses_splitk(const CDesc &d);
 
 }  // namespace tn

@@ -61,7 +61,7 @@ static LCount merge_counts(const LCount &x, const LCount &y) {
     return r;
 }
 
-std::string build_plan(const Net &net, const Tree &tree, Plan &plan) {
+std::string build_plan(const Net &net, const Tree &tree, Plan &plan, int64_t gemm_min) {
     std::string err = validate_tree(tree);
     if (!err.empty()) return err;
     int n = tree.nleaves;
@@ -117,14 +117,58 @@ std::string build_plan(const Net &net, const Tree &tree, Plan &plan) {
         for (int v : la)
             if (kept.count(v)) nd.labels.push_back(v);
         nd.beta = plan.node[a].beta || plan.node[b].beta;
+        // GEMM form: groups bt (in both, kept), m (row operand only, kept),
+        // n (column operand only, kept), k (in both, summed); the operand
+        // holding the batch label goes on the row side so that the label
+        // stays outermost in C = [bt, m, n].
+        if (gemm_min > 0) {
+            int ga = a, gb = b;
+            if (plan.node[b].beta && !plan.node[a].beta) std::swap(ga, gb);
+            const Labels &xa = plan.node[ga].labels, &xb = plan.node[gb].labels;
+            std::set<int> sxa(xa.begin(), xa.end()), sxb(xb.begin(), xb.end());
+            Labels gbt, gm, gn, gk;
+            bool onesided = false;
+            for (int v : xa) {
+                if (kept.count(v)) (sxb.count(v) ? gbt : gm).push_back(v);
+                else if (sxb.count(v)) gk.push_back(v);
+                else onesided = true;
+            }
+            for (int v : xb) {
+                if (kept.count(v) && !sxa.count(v)) gn.push_back(v);
+                else if (!kept.count(v) && !sxa.count(v)) onesided = true;
+            }
+            auto prod = [&](const Labels &l) {
+                int64_t p = 1;
+                for (int v : l) p *= net.card[v];
+                return p;
+            };
+            if (!onesided && prod(gm) >= gemm_min && prod(gn) >= gemm_min &&
+                prod(gk) >= gemm_min) {
+                nd.gemm = true;
+                nd.ga = ga;
+                nd.gb = gb;
+                nd.gbt = gbt;
+                nd.gm = gm;
+                nd.gn = gn;
+                nd.labels.clear();
+                for (int v : gbt) nd.labels.push_back(v);
+                for (int v : gm) nd.labels.push_back(v);
+                for (int v : gn) nd.labels.push_back(v);
+            }
+        }
         nd.size = 1;
         for (int v : nd.labels) nd.size *= net.card[v];
         // eliminated labels in kernel order: a's order, then b-only labels
         nd.elim.clear();
-        for (int v : la)
-            if (!kept.count(v)) nd.elim.push_back(v);
-        for (int v : lb)
-            if (!sa.count(v) && !kept.count(v)) nd.elim.push_back(v);
+        if (nd.gemm) {
+            for (int v : plan.node[nd.ga].labels)
+                if (!kept.count(v)) nd.elim.push_back(v);
+        } else {
+            for (int v : la)
+                if (!kept.count(v)) nd.elim.push_back(v);
+            for (int v : lb)
+                if (!sa.count(v) && !kept.count(v)) nd.elim.push_back(v);
+        }
         double mul = 1;
         for (auto &p : cnt[me]) mul *= net.card[p.first];
         nd.muladds = mul;

@@ -87,32 +87,43 @@ void launch_leaves(const LeafRec *recs, int nrec, const double *tables, const in
 // log p(e_b) = ln(root_b) + ln2 * sum over every non-root tensor t of e_t(b),
 // where e_t is the binary exponent removed when t was consumed.  sigma_out
 // (optional) receives the log2 scale sum itself.
+// One block per batch item; the exponents are integers, so the block-wide
+// sum is exact in any order.
 template <typename T>
-__global__ void k_logz(int nbeta, const T *root, int root_beta, const unsigned long long *mx,
-                       const int64_t *exps, int nexp, double *logz, double *sigma_out,
-                       int maxplus) {
-    int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nbeta) return;
-    double r = (double)root[root_beta ? b : 0];
+__global__ void __launch_bounds__(256) k_logz(int nbeta, const T *root, int root_beta,
+                                              const unsigned long long *mx, const int64_t *exps,
+                                              int nexp, double *logz, double *sigma_out,
+                                              int maxplus) {
+    const int b = blockIdx.x;
+    const double r = (double)root[root_beta ? b : 0];
     if (maxplus) {
-        logz[b] = r;
+        if (threadIdx.x == 0) logz[b] = r;
         return;
     }
-    double s = 0;
-    for (int i = 0; i < nexp; ++i) {
+    long long s = 0;
+    for (int i = threadIdx.x; i < nexp; i += blockDim.x) {
         int64_t idx = exps[2 * i], bs = exps[2 * i + 1];
-        s += (double)exp_bits(mx[idx + (bs ? b : 0)]);
+        s += exp_bits(mx[idx + (bs ? b : 0)]);
     }
-    if (sigma_out) sigma_out[b] = s;
-    logz[b] = r > 0 ? log(r) + s * 0.69314718055994530942 : -INFINITY;
+    __shared__ long long part[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        if (sigma_out) sigma_out[b] = (double)t;
+        logz[b] = r > 0 ? log(r) + (double)t * 0.69314718055994530942 : -INFINITY;
+    }
 }
 
 template <typename T>
 void launch_logz(int nbeta, const T *root, int root_beta, const unsigned long long *mx,
                  const int64_t *exps, int nexp, double *logz, double *sigma_out, int maxplus,
                  cudaStream_t st) {
-    k_logz<T><<<(nbeta + 127) / 128, 128, 0, st>>>(nbeta, root, root_beta, mx, exps, nexp,
-                                                   logz, sigma_out, maxplus);
+    k_logz<T><<<nbeta, 256, 0, st>>>(nbeta, root, root_beta, mx, exps, nexp, logz, sigma_out,
+                                     maxplus);
 }
 
 // --------------------------------------------------------------- adjoints

@@ -39,6 +39,11 @@ struct Node {
     double muladds = 0;   // prod over the union of operand labels (per item)
     int parent = -1;
     int depth = 0;
+    // dense GEMM form C[bt, m, n] = sum_k A[bt, m, k] B[bt, k, n], chosen when
+    // every group is large and no label is summed inside one operand alone
+    bool gemm = false;
+    int ga = -1, gb = -1; // operand on the row (m) side, on the column (n) side
+    Labels gbt, gm, gn;   // batch, row and column labels (elim holds k)
 };
 
 struct Plan {
@@ -51,7 +56,9 @@ struct Plan {
 };
 
 std::string validate_tree(const Tree &t);
-std::string build_plan(const Net &net, const Tree &tree, Plan &plan);
+// gemm_min: a node takes the GEMM form when its m, n and k groups each hold
+// at least gemm_min entries per item (0 disables the GEMM form).
+std::string build_plan(const Net &net, const Tree &tree, Plan &plan, int64_t gemm_min = 0);
 Tree greedy_tree(const Net &net);
 Tree tree_from_elimination(const Net &net, const std::vector<int> &order);
 Tree optimize_tree(const Net &net, int method, int restarts, uint64_t seed);

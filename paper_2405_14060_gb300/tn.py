@@ -22,7 +22,9 @@ STATUS = {0: "TN_OK", 1: "TN_E_ARG", 2: "TN_E_PARSE", 3: "TN_E_ORDER", 4: "TN_E_
 EXPORTS = ["tn_load_model", "tn_load_model_arrays", "tn_free_model", "tn_set_order",
            "tn_tree_from_elimination", "tn_optimize_order", "tn_tree_stats", "tn_pr",
            "tn_mar", "tn_map", "tn_mmap", "tn_sample", "tn_pr_dev", "tn_mar_dev",
-           "tn_last_device_ms", "tn_last_launch_count", "tn_last_error", "tn_contract_dev"]
+           "tn_last_device_ms", "tn_last_launch_count", "tn_last_error", "tn_contract_dev",
+           "tn_profile", "tn_profile_steps"]
+PROFILE_CLASSES = ["small", "absorb", "reduce", "tcgemm", "simtgemm", "prep", "generic", "unused7"]
 
 
 class TNError(RuntimeError):
@@ -66,6 +68,8 @@ def lib():
             "tn_pr_dev": [P, I, P, P, I, P, P],
             "tn_mar_dev": [P, I, P, P, I, P, P, P, P],
             "tn_contract_dev": [I, P, I, P, P, I, P, P, I, P, P, I, I, I, P, P],
+            "tn_profile": [P, I, I, P, P, I, P],
+            "tn_profile_steps": [P, I, I, P, P, I, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -259,6 +263,35 @@ class Model:
                              None if tables is None else tables.data_ptr(),
                              1 if tables_are_log else 0, ctypes.byref(o), logz.data_ptr(),
                              marg.data_ptr(), None if grad is None else grad.data_ptr()))
+
+    def profile(self, task="mar", evid=None, batch=1, prec="tf32", reps=3):
+        """Per kernel class: ms, launches, FLOPs, bytes of one pass (averaged)."""
+        e = None if evid is None else np.ascontiguousarray(evid, np.int32).reshape(-1, self.nvars)
+        b = batch if e is None else e.shape[0]
+        out = np.zeros(32)
+        o = _opts(prec)
+        _ck(lib().tn_profile(self._h, 0 if task == "pr" else 1, b,
+                             None if e is None else _ptr(e), ctypes.byref(o), reps, _ptr(out)))
+        res = {}
+        for i, name in enumerate(PROFILE_CLASSES):
+            ms, n, fl, by = out[4 * i:4 * i + 4]
+            if n:
+                res[name] = {"ms": ms, "launches": n, "flops": fl, "bytes": by}
+        return res
+
+    def profile_steps(self, task="mar", evid=None, batch=1, prec="tf32", cap=100000):
+        """Per launch (launch order): class name, ms, FLOPs, bytes."""
+        e = None if evid is None else np.ascontiguousarray(evid, np.int32).reshape(-1, self.nvars)
+        b = batch if e is None else e.shape[0]
+        out = np.zeros(cap * 4)
+        n = ctypes.c_int()
+        o = _opts(prec)
+        _ck(lib().tn_profile_steps(self._h, 0 if task == "pr" else 1, b,
+                                   None if e is None else _ptr(e), ctypes.byref(o), cap,
+                                   _ptr(out), ctypes.byref(n)))
+        k = min(n.value, cap)
+        rows = out[:4 * k].reshape(k, 4)
+        return [(PROFILE_CLASSES[int(r[0])], r[1], r[2], r[3]) for r in rows]
 
     def last_device_ms(self) -> float:
         return float(lib().tn_last_device_ms(self._h))

@@ -95,10 +95,20 @@ def test_workload1_full():
     lz, marg = M.mar(prec="fp64")
     assert abs(lz[0] - lz_ref) < 1e-10
     _marg_close(M, marg[0], marg_ref, 1e-10)
+    assert abs(M.pr(prec="fp64")[0] - lz_ref) < 1e-10
     for prec in ("fp32", "tf32", "bf16"):
         lz2, marg2 = M.mar(prec=prec)
         assert abs(lz2[0] - lz_ref) <= 1e-4 * abs(lz_ref), prec
         _marg_close(M, marg2[0], marg_ref, 1e-3)
+        assert abs(M.pr(prec=prec)[0] - lz_ref) <= 1e-4 * abs(lz_ref), prec
+    # a second tree (min-fill elimination) with different micro / streaming splits
+    M.set_order(*M.optimize_order(1, 4, 11))
+    for prec in ("fp64", "fp32"):
+        tol = 1e-10 if prec == "fp64" else 1e-4 * abs(lz_ref)
+        assert abs(M.pr(prec=prec)[0] - lz_ref) <= tol
+        lz3, marg3 = M.mar(prec=prec)
+        assert abs(lz3[0] - lz_ref) <= tol
+        _marg_close(M, marg3[0], marg_ref, 1e-10 if prec == "fp64" else 1e-3)
 
 
 def test_map_small_and_workload3():
@@ -210,3 +220,37 @@ def test_contract_dev_matches_definition(case, dtype):
         np.testing.assert_array_equal(am.cpu().numpy().reshape(np.shape(ref_i)), ref_i)
     else:
         np.testing.assert_allclose(gv, ref_v, rtol=0, atol=1e-4 * max(1, np.abs(ref_v).max()))
+
+
+# ----------------------------------------------------------- GEMM form
+# sizes, labels A, labels B, labels C: every group >= 64 so the GEMM path runs
+GEMM_CASES = [
+    ([2] * 24, list(range(16)), list(range(8, 24)), list(range(8)) + list(range(16, 24))),
+    # ragged groups (m = 65, n = 111, k = 77), a batch label of size 3
+    ([5, 13, 3, 37, 7, 11, 3], [6, 0, 1, 4, 5], [6, 4, 5, 2, 3], [6, 0, 1, 2, 3]),
+    # output in a non-canonical order (n before m): scatter through a workspace
+    ([4, 4, 4, 4, 4, 4, 2], [0, 1, 2, 3], [2, 3, 4, 5, 6], [4, 5, 6, 0, 1]),
+    # several tiles in every direction: m = 512, n = 768, k = 384
+    ([8, 64, 3, 256, 128, 3], [0, 1, 4, 5], [4, 5, 2, 3], [0, 1, 2, 3]),
+]
+GEMM_TOL = {"fp64": 1e-12, "fp32": 1e-5, "tf32": 2e-3, "bf16": 1.5e-2}
+
+
+@pytest.mark.parametrize("case", range(len(GEMM_CASES)))
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16"])
+def test_gemm_form_matches_definition(case, prec):
+    sizes, la, lb, lc = GEMM_CASES[case]
+    rng = np.random.default_rng(100 + case)
+    A = rng.random([sizes[v] for v in la])
+    B = rng.random([sizes[v] for v in lb])
+    ref = np.einsum(A, la, B, lb, lc)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    tA = torch.tensor(A, dtype=dt, device="cuda").contiguous()
+    tB = torch.tensor(B, dtype=dt, device="cuda").contiguous()
+    tC = torch.zeros([sizes[v] for v in lc], dtype=dt, device="cuda")
+    for _ in range(2):      # twice: workspaces and pipeline state are reused cleanly
+        tC.zero_()
+        tn.contract_dev(sizes, la, tA, lb, tB, lc, tC, prec=prec)
+        got = tC.cpu().numpy()
+        err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+        assert err <= GEMM_TOL[prec], (prec, err)
