@@ -254,3 +254,36 @@ def test_gemm_form_matches_definition(case, prec):
         got = tC.cpu().numpy()
         err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
         assert err <= GEMM_TOL[prec], (prec, err)
+
+
+def test_autograd_factor_marginals():
+    """d log Z / d log T_f[x] is the factor marginal: a unary factor's equals
+    the oracle's variable marginal, each sums to one, and finite differences
+    of log Z agree."""
+    from paper_2405_14060_gb300.autograd import log_partition
+    m = synth.grid_ising(4, 21)
+    M = tn.Model.from_synth(m)
+    ev = np.full(m.nvars, -1, np.int32)
+    ev[5] = 1
+    lz_ref, marg_ref = oracle.brute_mar(m, ev)
+    lt = torch.tensor(np.log(np.concatenate(m.tables)), dtype=torch.float64, device="cuda",
+                      requires_grad=True)
+    evt = torch.tensor(ev, device="cuda")
+    lz, marg = log_partition(M, lt, evt)
+    assert abs(lz.item() - lz_ref) < 1e-10
+    lz.sum().backward()
+    g = lt.grad.cpu().numpy()
+    off = np.cumsum([0] + [len(t) for t in m.tables])
+    for f, sc in enumerate(m.scopes):
+        gf = g[off[f]:off[f + 1]]
+        assert abs(gf.sum() - 1.0) < 1e-10
+        if len(sc) == 1:
+            np.testing.assert_allclose(gf, marg_ref[int(sc[0])], atol=1e-10)
+    eps = 1e-6
+    base = lt.detach().clone()
+    for idx in (0, 7, off[-1] - 1):
+        up, dn = base.clone(), base.clone()
+        up[idx] += eps
+        dn[idx] -= eps
+        fd = (log_partition(M, up, evt)[0].item() - log_partition(M, dn, evt)[0].item()) / (2 * eps)
+        assert abs(fd - g[idx]) < 1e-7
