@@ -247,6 +247,44 @@ tn_status tn_contract_dev(int nlabels, const int *sizes,
                           int semiring, int dtype, tn_prec prec, int32_t *argmax,
                           void *cuda_stream);
 
+/* ------------------------------------------------ allocation-free variant */
+
+/* Size of the fixed device scratch used by tn_contract_dev_noalloc. */
+#define TN_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/*
+ * The same pairwise contraction as tn_contract_dev (same arguments, same
+ * results up to floating-point summation order), always on the split-K
+ * strided kernels, without allocating any device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot let a library
+ * allocate GPU memory -- an application that owns all device memory through
+ * its own pool, or a latency-critical loop where cudaMalloc / cudaFree, which
+ * may synchronise the device, are not acceptable.
+ *
+ * The split-K partial sums live in one file-scope device array of
+ * TN_NOALLOC_SCRATCH_BYTES bytes that every GPU loading the library holds
+ * until the process exits.  An output whose partials cannot fit even with a
+ * single K chunk per output entry (more than TN_NOALLOC_SCRATCH_BYTES /
+ * (element size + 4) entries) is rejected with TN_E_ARG and a message naming
+ * the limit; nothing is launched then.
+ *
+ * The first call on each device looks up the array's device address (once,
+ * with that device current), so make the first call on a device before any
+ * stream capture.  All calls in the process share the array and it keeps the
+ * last call's contents (no part of it needs to start at zero: a call reads
+ * only partials it wrote itself).  Calls whose kernels can overlap on the GPU
+ * -- on different streams without ordering, or from several host threads --
+ * race on the array and must be serialised by the caller.  The call
+ * synchronises `cuda_stream` before returning.  prec is not taken: the
+ * split-K kernels compute in the data type (dtype 0 double, 1 float).
+ */
+tn_status tn_contract_dev_noalloc(int nlabels, const int *sizes,
+                                  int na, const int *labels_a, const void *A,
+                                  int nb, const int *labels_b, const void *B,
+                                  int nc, const int *labels_c, void *C,
+                                  int semiring, int dtype, int32_t *argmax,
+                                  void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

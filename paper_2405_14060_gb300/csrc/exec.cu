@@ -1570,6 +1570,45 @@ tn_status override_tables(tn_model *m, const double *dev_tables, int is_log, cud
 
 }  // namespace
 
+namespace tn {
+// Used by other translation units of the library (declared where used).
+tn_status set_error(tn_status s, const std::string &msg) { return fail(s, msg); }
+
+// Descriptor of one plain pairwise contraction (no rescaling) on caller data.
+tn_status plain_contract_desc(int nlabels, const int *sizes, int na, const int *labels_a,
+                              const void *A, int nb, const int *labels_b, const void *B, int nc,
+                              const int *labels_c, void *C, int semiring, int32_t *argmax,
+                              CDesc &d) {
+    if (nlabels < 0 || !sizes || (na && !labels_a) || (nb && !labels_b) || (nc && !labels_c) ||
+        !A || !B || !C)
+        return fail(TN_E_ARG, "NULL argument");
+    if (semiring != 0 && semiring != 1) return fail(TN_E_ARG, "semiring must be 0 or 1");
+    std::vector<int> card(sizes, sizes + nlabels);
+    for (int c : card)
+        if (c < 1) return fail(TN_E_ARG, "label size < 1");
+    auto chk = [&](int n, const int *l, Labels &out) -> bool {
+        std::set<int> seen;
+        for (int i = 0; i < n; ++i) {
+            if (l[i] < 0 || l[i] >= nlabels || seen.count(l[i])) return false;
+            seen.insert(l[i]);
+            out.push_back(l[i]);
+        }
+        return true;
+    };
+    Labels la, lb, lc;
+    if (!chk(na, labels_a, la) || !chk(nb, labels_b, lb) || !chk(nc, labels_c, lc))
+        return fail(TN_E_ARG, "labels out of range or repeated");
+    std::set<int> u(la.begin(), la.end());
+    u.insert(lb.begin(), lb.end());
+    for (int v : lc)
+        if (!u.count(v)) return fail(TN_E_ARG, "output label in neither operand");
+    std::string err = make_desc(card, la, false, 0, A, nullptr, lb, false, 0, B, nullptr, lc,
+                                false, C, nullptr, nullptr, 1, semiring == 1 ? argmax : nullptr, d);
+    if (!err.empty()) return fail(TN_E_UNSUPPORTED, err);
+    return TN_OK;
+}
+}  // namespace tn
+
 // =================================================================== C ABI
 
 extern "C" {

@@ -293,6 +293,47 @@ void launch_contract(const CDesc &d, int semiring, void *scratch, size_t scratch
     if (nlaunch) *nlaunch += 1;
 }
 
+// Split-K contraction into a fixed scratch buffer of `cap` bytes: the number
+// of K chunks is the one launch_contract would pick, lowered until the
+// partial results fit.  Returns false (launching nothing) when even one chunk
+// per output does not fit.
+template <typename T>
+bool launch_contract_splitk_fixed(const CDesc &d, int semiring, void *scratch, size_t cap,
+                                  cudaStream_t st) {
+    int64_t total = d.nout_total * d.nbeta;
+    if (total == 0) return true;
+    int64_t chunk;
+    int nchunks;
+    splitk_shape(d, chunk, nchunks);
+    auto need = [&](int nc) {
+        size_t pb = ((size_t)(total * nc) * sizeof(T) + 255) & ~(size_t)255;
+        return pb + (size_t)(total * nc) * 4;
+    };
+    while (nchunks > 1 && need(nchunks) > cap) {
+        nchunks = (nchunks + 1) / 2;
+        chunk = (d.ktotal + nchunks - 1) / nchunks;
+        nchunks = (int)((d.ktotal + chunk - 1) / chunk);
+    }
+    if (need(nchunks) > cap) return false;
+    size_t pb = ((size_t)(total * nchunks) * sizeof(T) + 255) & ~(size_t)255;
+    T *part = (T *)scratch;
+    int32_t *pidx = (int32_t *)((char *)scratch + pb);
+    dim3 grid((unsigned)nchunks, (unsigned)std::min<int64_t>(total, 65535),
+              (unsigned)((total + 65534) / 65535));
+    if (semiring == SUM)
+        k_contract_splitk<T, SUM><<<grid, 256, 0, st>>>(d, chunk, nchunks, part, pidx);
+    else
+        k_contract_splitk<T, MAXPLUS><<<grid, 256, 0, st>>>(d, chunk, nchunks, part, pidx);
+    unsigned rb = (unsigned)((total + 255) / 256);
+    if (semiring == SUM) k_splitk_reduce<T, SUM><<<rb, 256, 0, st>>>(d, nchunks, part, pidx);
+    else k_splitk_reduce<T, MAXPLUS><<<rb, 256, 0, st>>>(d, nchunks, part, pidx);
+    return true;
+}
+
+template bool launch_contract_splitk_fixed<float>(const CDesc &, int, void *, size_t, cudaStream_t);
+template bool launch_contract_splitk_fixed<double>(const CDesc &, int, void *, size_t,
+                                                   cudaStream_t);
+
 template void launch_contract<float>(const CDesc &, int, void *, size_t, cudaStream_t, int *);
 template void launch_contract<double>(const CDesc &, int, void *, size_t, cudaStream_t, int *);
 

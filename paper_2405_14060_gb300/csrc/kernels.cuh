@@ -42,5 +42,8 @@ void launch_contract(const CDesc &d, int semiring, void *scratch, size_t scratch
                      cudaStream_t st, int *nlaunch);
 size_t contract_scratch_bytes(const CDesc &d, int elem_bytes);
 bool contract_uses_splitk(const CDesc &d);
+template <typename T>
+bool launch_contract_splitk_fixed(const CDesc &d, int semiring, void *scratch, size_t cap,
+                                  cudaStream_t st);
 
 }  // namespace tn

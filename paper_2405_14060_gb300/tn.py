@@ -23,7 +23,7 @@ EXPORTS = ["tn_load_model", "tn_load_model_arrays", "tn_free_model", "tn_set_ord
            "tn_tree_from_elimination", "tn_optimize_order", "tn_tree_stats", "tn_pr",
            "tn_mar", "tn_map", "tn_mmap", "tn_sample", "tn_pr_dev", "tn_mar_dev",
            "tn_last_device_ms", "tn_last_launch_count", "tn_last_error", "tn_contract_dev",
-           "tn_profile", "tn_profile_steps"]
+           "tn_profile", "tn_profile_steps", "tn_contract_dev_noalloc"]
 PROFILE_CLASSES = ["small", "absorb", "reduce", "tcgemm", "simtgemm", "prep", "generic", "unused7"]
 
 
@@ -70,6 +70,7 @@ def lib():
             "tn_contract_dev": [I, P, I, P, P, I, P, P, I, P, P, I, I, I, P, P],
             "tn_profile": [P, I, I, P, P, I, P],
             "tn_profile_steps": [P, I, I, P, P, I, P, P],
+            "tn_contract_dev_noalloc": [I, P, I, P, P, I, P, P, I, P, P, I, I, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -313,3 +314,18 @@ def contract_dev(sizes, la, A, lb, B, lc, C, semiring=0, argmax=None, prec="fp32
                               B.data_ptr(), len(c), _ptr(c) if len(c) else None, C.data_ptr(),
                               semiring, dtype, PRECS[prec],
                               None if argmax is None else argmax.data_ptr(), stream))
+
+
+def contract_dev_noalloc(sizes, la, A, lb, B, lc, C, semiring=0, argmax=None, stream=None):
+    """tn_contract_dev_noalloc: the same contraction as contract_dev without
+    any device allocation (split-K partials in the library's fixed scratch)."""
+    import torch
+    dtype = 0 if A.dtype == torch.float64 else 1
+    sz = np.ascontiguousarray(sizes, np.int32)
+    a = np.ascontiguousarray(la, np.int32)
+    b = np.ascontiguousarray(lb, np.int32)
+    c = np.ascontiguousarray(lc, np.int32)
+    _ck(lib().tn_contract_dev_noalloc(len(sz), _ptr(sz), len(a), _ptr(a), A.data_ptr(), len(b),
+                                      _ptr(b), B.data_ptr(), len(c), _ptr(c) if len(c) else None,
+                                      C.data_ptr(), semiring, dtype,
+                                      None if argmax is None else argmax.data_ptr(), stream))
