@@ -106,9 +106,15 @@ void tn_free_model(tn_model *m);
  *
  * nnodes = 0 with left = right = NULL selects the built-in greedy order
  * (repeatedly contract the connected pair with the smallest size increase).
- * slice_vars[0..nslice) are variables fixed per slice: the tree is contracted
- * once per assignment of them and the results are combined (log-sum-exp for
- * PR, weighted sums for MAR).  Errors: TN_E_ORDER (a malformed tree).
+ * slice_vars[0..nslice) are variables fixed per slice: they are removed from
+ * every tensor, the tree is contracted once per assignment of them (at most
+ * 2^24 assignments) and the results are combined on the device: log-sum-exp
+ * of log Z for PR, Z-weighted marginals for MAR (a sliced variable's
+ * marginal is the Z-share of its values).  Slicing bounds the largest
+ * intermediate by the product of the sliced domains; MPE, MMAP and sampling
+ * reject a sliced tree (TN_E_UNSUPPORTED).  tn_tree_stats then reports the
+ * per-slice space complexity and the total time over all slices.
+ * Errors: TN_E_ORDER (a malformed tree), TN_E_ARG (bad slice variables).
  */
 tn_status tn_set_order(tn_model *m, int nnodes, const int *left, const int *right,
                        int nslice, const int *slice_vars);
@@ -123,7 +129,12 @@ tn_status tn_tree_from_elimination(const tn_model *m, int nelim, const int *orde
 /* Search a contraction tree: method 0 = greedy (as tn_set_order's default),
  * 1 = randomised min-fill / min-degree elimination with `restarts` restarts
  * keeping the tree of least time complexity whose space complexity is
- * minimal.  Writes nleaves-1 entries to left/right. */
+ * minimal, 2 = method 1 followed by `restarts` rounds of simulated annealing
+ * over local rotations of the tree (objective: log2 of the total
+ * multiply-add count plus a penalty on space complexity above the best seen
+ * minus one), in the spirit of the tree-annealing finders the paper cites for
+ * its orders (Sec. Tensor networks).  Host only; deterministic for a seed.
+ * Writes nleaves-1 entries to left/right. */
 tn_status tn_optimize_order(const tn_model *m, int method, int restarts, uint64_t seed,
                             int *left, int *right);
 
@@ -139,7 +150,10 @@ tn_status tn_tree_stats(const tn_model *m, int batch, tn_prec prec, double *out)
 /* ------------------------------------------------------------- tasks */
 
 /* PR: logz[b] = log p(e_b) for each of `batch` evidence sets evid[b][nvars]
- * (Eq. pr).  log p(e) = -inf when the evidence is impossible. */
+ * (Eq. pr).  log p(e) = -inf when the evidence is impossible.  The evidence
+ * sets run as one batched contraction (a batch label on every unity vector);
+ * when that does not fit the device memory or opts->hbm_budget_bytes, they
+ * run in the largest power-of-two sub-batches that do (same for tn_mar). */
 tn_status tn_pr(tn_model *m, int batch, const int32_t *evid, const tn_options *opts,
                 double *logz);
 

@@ -39,8 +39,11 @@ static tn_status fail(tn_status s, const std::string &msg) {
 #define CK(call)                                                                          \
     do {                                                                                  \
         cudaError_t e_ = (call);                                                          \
-        if (e_ != cudaSuccess)                                                            \
-            return fail(TN_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));  \
+        if (e_ != cudaSuccess) {                                                          \
+            if (e_ == cudaErrorMemoryAllocation) cudaGetLastError();                      \
+            return fail(e_ == cudaErrorMemoryAllocation ? TN_E_OOM : TN_E_CUDA,           \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));              \
+        }                                                                                 \
     } while (0)
 
 namespace {
@@ -158,6 +161,7 @@ struct Program {
     double *cdf = nullptr;
     std::vector<std::pair<CDesc, int64_t>> cdf_nodes;
     int32_t *d_evid = nullptr;
+    int32_t *d_slice_val = nullptr;     // values of the sliced variables for this run
     double *d_logz = nullptr, *d_sigma = nullptr, *d_marg = nullptr, *d_grad = nullptr;
     int32_t *d_assign = nullptr;
     int *d_card = nullptr;
@@ -186,6 +190,11 @@ struct tn_model {
     Tree tree;
     bool has_tree = false;
     std::vector<int> slice_vars;
+    // slice combination buffers (device): running max / sum / weighted marginals
+    double *d_sM = nullptr, *d_sS = nullptr, *d_sA = nullptr;
+    int64_t s_cap_b = 0, s_cap_m = 0;
+    int32_t *d_sl_var = nullptr, *d_sl_card = nullptr, *d_sl_tab = nullptr;
+    int64_t *d_sl_moff = nullptr;
     double *d_tables = nullptr;
     int *d_flags = nullptr;            // [0]: tables hold logarithms
     int *d_err = nullptr;              // set by a device-side wait that gave up
@@ -198,6 +207,9 @@ struct tn_model {
     int64_t last_launches = 0;
     ~tn_model() {
         progs.clear();
+        for (void *p : {(void *)d_sM, (void *)d_sS, (void *)d_sA, (void *)d_sl_var,
+                        (void *)d_sl_card, (void *)d_sl_tab, (void *)d_sl_moff})
+            if (p) cudaFree(p);
         if (d_tables) cudaFree(d_tables);
         if (d_flags) cudaFree(d_flags);
         if (d_err) cudaFree(d_err);
@@ -209,15 +221,23 @@ struct tn_model {
 
 namespace {
 
-Net model_net(const ModelData &md, bool batched) {
+// The model's network: factor leaves, then one unity / evidence vector per
+// variable.  Sliced variables are removed from every leaf (their values are
+// fixed per slice).
+Net model_net(const ModelData &md, bool batched, const std::vector<int> &sliced = {}) {
     Net n;
     n.card = md.card;
+    std::vector<char> sl(md.nvars, 0);
+    for (int v : sliced) sl[v] = 1;
     for (int f = 0; f < md.nfactors; ++f) {
-        n.leaf.push_back(md.scope[f]);
+        Labels l;
+        for (int v : md.scope[f])
+            if (!sl[v]) l.push_back(v);
+        n.leaf.push_back(l);
         n.leaf_beta.push_back(0);
     }
     for (int v = 0; v < md.nvars; ++v) {
-        n.leaf.push_back({v});
+        n.leaf.push_back(sl[v] ? Labels{} : Labels{v});
         n.leaf_beta.push_back(batched ? 1 : 0);
     }
     return n;
@@ -895,6 +915,8 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
     CK(P.mem.alloc(&P.mx, (size_t)nmx * 8));
     if (am_total) CK(P.mem.alloc(&P.am, (size_t)am_total * 4));
     CK(P.mem.alloc(&P.d_evid, (size_t)nbeta * std::max(1, m->md.nvars) * 4));
+    CK(P.mem.alloc(&P.d_slice_val, 4 * std::max<size_t>(1, m->slice_vars.size())));
+    CK(cudaMemset(P.d_slice_val, 0, 4 * std::max<size_t>(1, m->slice_vars.size())));
     CK(P.mem.alloc(&P.d_logz, (size_t)nbeta * 8));
     CK(P.mem.alloc(&P.d_sigma, (size_t)nbeta * 8));
     CK(P.mem.alloc(&P.d_card, net.card.size() * 4 + 4));
@@ -904,16 +926,42 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
     for (int id = 0; id < n; ++id) {
         LeafRec r;
         std::memset(&r, 0, sizeof r);
+        r.nkd = -1;
+        r.slice_of_var = -1;
         if (spec) {
             r = (*spec)[id];
+            r.nkd = -1;
+            r.slice_of_var = -1;
             if (r.kind == LEAF_UNITY) r.beta = pl.node[id].beta;
         } else if (id < (int)m->md.nfactors) {
             r.kind = LEAF_FACTOR;
             r.src = m->md.toff[id];
+            const Labels &full = m->md.scope[id];
+            if (full.size() != net.leaf[id].size()) {
+                // sliced factor: gather the kept labels at the slice values
+                if (full.size() > (size_t)LEAF_D)
+                    return fail(TN_E_UNSUPPORTED, "sliced factor with more than 16 variables");
+                r.nkd = 0;
+                r.nsd = 0;
+                for (int v : full) {
+                    int64_t st = stride_in(m->md.card, full, v);
+                    auto it = std::find(m->slice_vars.begin(), m->slice_vars.end(), v);
+                    if (it != m->slice_vars.end()) {
+                        r.sidx[r.nsd] = (int32_t)(it - m->slice_vars.begin());
+                        r.sst[r.nsd++] = st;
+                    } else {
+                        r.ksz[r.nkd] = m->md.card[v];
+                        r.kst[r.nkd++] = st;
+                    }
+                }
+            }
         } else {
+            int v = id - m->md.nfactors;
             r.kind = LEAF_UNITY;
-            r.var = net.leaf[id].empty() ? 0 : net.leaf[id][0];
+            r.var = v;
             r.beta = pl.node[id].beta;
+            auto it = std::find(m->slice_vars.begin(), m->slice_vars.end(), v);
+            if (it != m->slice_vars.end()) r.slice_of_var = (int)(it - m->slice_vars.begin());
         }
         r.size = P.fwd[id].per;
         r.dst = P.fwd[id].off;
@@ -1201,6 +1249,8 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
             r.card = m->md.card[v];
             r.fbeta = P.fwd[id].beta;
             r.abeta = P.adj_beta[id];
+            r.sliced = std::find(m->slice_vars.begin(), m->slice_vars.end(), v) !=
+                       m->slice_vars.end();
             moff += r.card;
             mr.push_back(r);
         }
@@ -1376,7 +1426,7 @@ void enqueue_program(tn_model *m, Program &P, cudaStream_t st, Prof *pr = nullpt
     cudaMemsetAsync(P.mx, 0, (size_t)P.nmx * 8, st);
     ++nl;
     launch_leaves<T>(P.d_leaf, P.nleafrec, m->d_tables, P.d_card, m->md.nvars, P.d_evid, P.nbeta,
-                     maxplus ? 1 : 0, (T *)P.arena, P.mx, m->d_flags, st);
+                     maxplus ? 1 : 0, (T *)P.arena, P.mx, m->d_flags, P.d_slice_val, st);
     ++nl;
     if (!P.mf.empty()) {
         timed(pr, st, C_SMALL, 0, 0, [&] {
@@ -1491,8 +1541,14 @@ tn_status get_program(tn_model *m, int kind, int nbeta, const tn_options *opts, 
         return TN_OK;
     }
     auto P = std::make_unique<Program>();
-    Net net = model_net(m->md, nbeta > 1);
+    Net net = model_net(m->md, nbeta > 1, m->slice_vars);
     s = build_program(m, net, m->tree, kind, dtype, nbeta, grads, opts, *P);
+    if (s == TN_E_OOM && !m->progs.empty()) {
+        // release the other cached programs of this model and try once more
+        m->progs.clear();
+        P = std::make_unique<Program>();
+        s = build_program(m, net, m->tree, kind, dtype, nbeta, grads, opts, *P);
+    }
     if (s) return s;
     s = capture_program(m, *P);
     if (s) return s;
@@ -1525,14 +1581,16 @@ tn_status check_device_error(tn_model *m) {
 
 // Run a captured program: copy the evidence in, replay the graph, time it.
 tn_status run_program(tn_model *m, Program &P, const int32_t *evid, bool evid_on_device,
-                      cudaStream_t st, bool sync = true) {
-    size_t eb = (size_t)P.nbeta * m->md.nvars * 4;
+                      cudaStream_t st, bool sync = true, int nrows = -1) {
+    if (nrows < 0) nrows = P.nbeta;
+    size_t row = (size_t)m->md.nvars * 4, eb = (size_t)P.nbeta * row;
     if (eb) {
-        if (evid)
-            CK(cudaMemcpyAsync(P.d_evid, evid, eb,
+        if (evid && nrows > 0)
+            CK(cudaMemcpyAsync(P.d_evid, evid, (size_t)nrows * row,
                                evid_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
-        else
-            CK(cudaMemsetAsync(P.d_evid, 0xff, eb, st));
+        if (!evid || nrows < P.nbeta)
+            CK(cudaMemsetAsync((char *)P.d_evid + (evid ? (size_t)nrows * row : 0), 0xff,
+                               eb - (evid ? (size_t)nrows * row : 0), st));
     }
     if (!sync) {
         CK(cudaGraphLaunch(P.gexec, st));
@@ -1547,6 +1605,93 @@ tn_status run_program(tn_model *m, Program &P, const int32_t *evid, bool evid_on
     CK(cudaEventElapsedTime(&ms, m->ev0, m->ev1));
     m->last_ms = ms;
     m->last_launches = P.launches;
+    CK(cudaGetLastError());
+    return check_device_error(m);
+}
+
+// Number of slice assignments and (lazily) the device table of all of them,
+// last sliced variable fastest.
+tn_status slice_setup(tn_model *m, int64_t &nass) {
+    const auto &sl = m->slice_vars;
+    nass = 1;
+    for (int v : sl) nass *= m->md.card[v];
+    if (sl.empty() || m->d_sl_tab) return TN_OK;
+    std::vector<int32_t> tab((size_t)nass * sl.size()), var(sl.begin(), sl.end()), card;
+    std::vector<int64_t> moff;
+    int64_t acc = 0;
+    std::vector<int64_t> off(m->md.nvars);
+    for (int v = 0; v < m->md.nvars; ++v) {
+        off[v] = acc;
+        acc += m->md.card[v];
+    }
+    for (int v : sl) {
+        card.push_back(m->md.card[v]);
+        moff.push_back(off[v]);
+    }
+    for (int64_t a = 0; a < nass; ++a) {
+        int64_t r = a;
+        for (int j = (int)sl.size() - 1; j >= 0; --j) {
+            tab[(size_t)a * sl.size() + j] = (int32_t)(r % card[j]);
+            r /= card[j];
+        }
+    }
+    CK(cudaMalloc(&m->d_sl_tab, tab.size() * 4));
+    CK(cudaMemcpy(m->d_sl_tab, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&m->d_sl_var, var.size() * 4));
+    CK(cudaMemcpy(m->d_sl_var, var.data(), var.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&m->d_sl_card, card.size() * 4));
+    CK(cudaMemcpy(m->d_sl_card, card.data(), card.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&m->d_sl_moff, moff.size() * 8));
+    CK(cudaMemcpy(m->d_sl_moff, moff.data(), moff.size() * 8, cudaMemcpyHostToDevice));
+    return TN_OK;
+}
+
+// PR / MAR over every slice assignment: one graph replay per assignment and a
+// running log-sum-exp (and Z-weighted marginals) on the device; the results
+// land in the program's log Z / marginal buffers.
+tn_status run_sliced(tn_model *m, Program &P, const int32_t *evid, bool evid_dev, bool marg,
+                     cudaStream_t st, int nrows = -1) {
+    if (nrows < 0) nrows = P.nbeta;
+    int64_t nass;
+    tn_status s = slice_setup(m, nass);
+    if (s) return s;
+    const int nsl = (int)m->slice_vars.size();
+    int64_t nm = std::max<int64_t>(1, P.marg_stride);
+    if (P.nbeta > m->s_cap_b || nm > m->s_cap_m) {
+        for (double *p : {m->d_sM, m->d_sS, m->d_sA})
+            if (p) cudaFree(p);
+        m->s_cap_b = P.nbeta;
+        m->s_cap_m = nm;
+        CK(cudaMalloc(&m->d_sM, (size_t)P.nbeta * 8));
+        CK(cudaMalloc(&m->d_sS, (size_t)P.nbeta * 8));
+        CK(cudaMalloc(&m->d_sA, (size_t)P.nbeta * nm * 8));
+    }
+    size_t row = (size_t)m->md.nvars * 4, eb = (size_t)P.nbeta * row;
+    if (eb) {
+        if (evid && nrows > 0)
+            CK(cudaMemcpyAsync(P.d_evid, evid, (size_t)nrows * row,
+                               evid_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+        if (!evid || nrows < P.nbeta)
+            CK(cudaMemsetAsync((char *)P.d_evid + (evid ? (size_t)nrows * row : 0), 0xff,
+                               eb - (evid ? (size_t)nrows * row : 0), st));
+    }
+    CK(cudaEventRecord(m->ev0, st));
+    launch_slice_init(P.nbeta, nm, m->d_sM, m->d_sS, m->d_sA, st);
+    for (int64_t a = 0; a < nass; ++a) {
+        CK(cudaMemcpyAsync(P.d_slice_val, m->d_sl_tab + a * nsl, (size_t)nsl * 4,
+                           cudaMemcpyDeviceToDevice, st));
+        CK(cudaGraphLaunch(P.gexec, st));
+        launch_slice_acc(P.nbeta, P.d_logz, marg ? P.d_marg : nullptr, nm, P.d_slice_val, nsl,
+                         m->d_sl_var, m->d_sl_moff, m->d_sl_card, m->d_sM, m->d_sS, m->d_sA, st);
+    }
+    launch_slice_fin(P.nbeta, nm, m->d_sM, m->d_sS, m->d_sA, P.d_logz, marg ? P.d_marg : nullptr,
+                     st);
+    CK(cudaEventRecord(m->ev1, st));
+    CK(cudaStreamSynchronize(st));
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, m->ev0, m->ev1));
+    m->last_ms = ms;
+    m->last_launches = (P.launches + 2) * nass + 2;
     CK(cudaGetLastError());
     return check_device_error(m);
 }
@@ -1660,15 +1805,30 @@ tn_status tn_set_order(tn_model *m, int nnodes, const int *left, const int *righ
         std::string err = validate_tree(t);
         if (!err.empty()) return fail(TN_E_ORDER, err);
     }
+    std::vector<int> sl;
     if (nslice > 0) {
         if (!slice_vars) return fail(TN_E_ARG, "NULL slice variables");
-        for (int i = 0; i < nslice; ++i)
-            if (slice_vars[i] < 0 || slice_vars[i] >= m->md.nvars)
-                return fail(TN_E_ARG, "slice variable out of range");
-        return fail(TN_E_UNSUPPORTED, "slicing is not supported by this build");
+        double nass = 1;
+        for (int i = 0; i < nslice; ++i) {
+            int v = slice_vars[i];
+            if (v < 0 || v >= m->md.nvars) return fail(TN_E_ARG, "slice variable out of range");
+            if (std::find(sl.begin(), sl.end(), v) != sl.end())
+                return fail(TN_E_ARG, "slice variable repeated");
+            sl.push_back(v);
+            nass *= m->md.card[v];
+        }
+        if (nass > (double)(1 << 24)) return fail(TN_E_ARG, "more than 2^24 slices");
     }
     m->tree = t;
     m->has_tree = true;
+    if (sl != m->slice_vars) {
+        for (void *p : {(void *)m->d_sl_var, (void *)m->d_sl_card, (void *)m->d_sl_tab,
+                        (void *)m->d_sl_moff})
+            if (p) cudaFree(p);
+        m->d_sl_var = m->d_sl_card = m->d_sl_tab = nullptr;
+        m->d_sl_moff = nullptr;
+    }
+    m->slice_vars = sl;
     m->progs.clear();
     return TN_OK;
 }
@@ -1688,7 +1848,7 @@ tn_status tn_tree_from_elimination(const tn_model *m, int nelim, const int *orde
 tn_status tn_optimize_order(const tn_model *m, int method, int restarts, uint64_t seed, int *left,
                             int *right) {
     if (!m || !left || !right) return fail(TN_E_ARG, "NULL argument");
-    if (method < 0 || method > 1) return fail(TN_E_ARG, "unknown method");
+    if (method < 0 || method > 2) return fail(TN_E_ARG, "unknown method");
     Tree t = optimize_tree(model_net(m->md, false), method, restarts, seed);
     std::copy(t.left.begin(), t.left.end(), left);
     std::copy(t.right.begin(), t.right.end(), right);
@@ -1697,10 +1857,12 @@ tn_status tn_optimize_order(const tn_model *m, int method, int restarts, uint64_
 
 tn_status tn_tree_stats(const tn_model *m, int batch, tn_prec prec, double *out) {
     if (!m || !out || batch < 1) return fail(TN_E_ARG, "bad argument");
-    Net net = model_net(m->md, batch > 1);
+    Net net = model_net(m->md, batch > 1, m->slice_vars);
     Tree t = m->has_tree ? m->tree : greedy_tree(model_net(m->md, false));
     Plan p;
     std::string err = build_plan(net, t, p);
+    double nass = 1;
+    for (int v : m->slice_vars) nass *= m->md.card[v];
     if (!err.empty()) return fail(TN_E_ORDER, err);
     int n = t.nleaves;
     double mul = 0, bytes = 0, sc = 0;
@@ -1714,6 +1876,8 @@ tn_status tn_tree_stats(const tn_model *m, int batch, tn_prec prec, double *out)
                        (double)nd.size * bt);
         sc = std::max(sc, std::log2((double)nd.size * bt));
     }
+    mul *= nass;
+    bytes *= nass;
     out[0] = mul > 0 ? std::log2(mul) : 0;
     out[1] = sc;
     out[2] = bytes > 0 ? std::log2(bytes / es) : 0;
@@ -1721,6 +1885,24 @@ tn_status tn_tree_stats(const tn_model *m, int batch, tn_prec prec, double *out)
     out[4] = 2 * mul;
     out[5] = bytes;
     return TN_OK;
+}
+
+// The program for `batch` evidence sets, or, when it does not fit the device
+// memory / HBM budget, for the largest power-of-two sub-batch that does.
+static tn_status program_fitting(tn_model *m, int kind, int batch, const tn_options *opts,
+                                 bool grads, Program **out, int *sub) {
+    int b = batch;
+    for (;;) {
+        tn_status s = get_program(m, kind, b, opts, grads, out);
+        if (s == TN_OK) {
+            *sub = b;
+            return TN_OK;
+        }
+        if (s != TN_E_OOM || b == 1) return s;
+        int p = 1;
+        while (p * 2 < b) p *= 2;
+        b = p;
+    }
 }
 
 static tn_status pr_common(tn_model *m, int batch, const int32_t *evid, bool evid_dev,
@@ -1732,17 +1914,29 @@ static tn_status pr_common(tn_model *m, int batch, const int32_t *evid, bool evi
         if (s) return s;
     }
     Program *P;
-    tn_status s = get_program(m, K_PR, batch, opts, false, &P);
+    int sub = batch;
+    tn_status s = program_fitting(m, K_PR, batch, opts, false, &P, &sub);
     if (s) return s;
     cudaStream_t st = stream_of(m, opts);
     s = override_tables(m, tables_dev, is_log, st);
     if (s) return s;
-    const bool async = evid_dev && opts && opts->cuda_stream;
-    s = run_program(m, *P, evid, evid_dev, st, !async);
-    if (s) return s;
-    CK(cudaMemcpyAsync(logz, P->d_logz, (size_t)batch * 8,
-                       logz_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
-    if (!async) CK(cudaStreamSynchronize(st));
+    const bool async =
+        evid_dev && opts && opts->cuda_stream && m->slice_vars.empty() && sub == batch;
+    double ms = 0;
+    for (int i = 0; i < batch; i += sub) {
+        int nr = std::min(sub, batch - i);
+        const int32_t *ev = evid ? evid + (size_t)i * m->md.nvars : nullptr;
+        s = m->slice_vars.empty() ? run_program(m, *P, ev, evid_dev, st, !async, nr)
+                                  : run_sliced(m, *P, ev, evid_dev, false, st, nr);
+        if (s) return s;
+        ms += m->last_ms;
+        CK(cudaMemcpyAsync(logz + i, P->d_logz, (size_t)nr * 8,
+                           logz_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    }
+    if (!async) {
+        CK(cudaStreamSynchronize(st));
+        m->last_ms = ms;
+    }
     return TN_OK;
 }
 
@@ -1764,20 +1958,32 @@ static tn_status mar_common(tn_model *m, int batch, const int32_t *evid, bool de
         if (s) return s;
     }
     Program *P;
-    tn_status s = get_program(m, K_MAR, batch, opts, grad != nullptr, &P);
+    int sub = batch;
+    tn_status s = program_fitting(m, K_MAR, batch, opts, grad != nullptr, &P, &sub);
     if (s) return s;
     cudaStream_t st = stream_of(m, opts);
     s = override_tables(m, tables_dev, is_log, st);
     if (s) return s;
-    const bool async = dev && opts && opts->cuda_stream;
-    s = run_program(m, *P, evid, dev, st, !async);
-    if (s) return s;
+    const bool async = dev && opts && opts->cuda_stream && m->slice_vars.empty() && sub == batch;
     cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    CK(cudaMemcpyAsync(logz, P->d_logz, (size_t)batch * 8, k, st));
-    CK(cudaMemcpyAsync(marg, P->d_marg, (size_t)batch * P->marg_stride * 8, k, st));
-    if (grad) CK(cudaMemcpyAsync(grad, P->d_grad, (size_t)batch * P->grad_stride * 8, k, st));
+    double ms = 0;
+    for (int i = 0; i < batch; i += sub) {
+        int nr = std::min(sub, batch - i);
+        const int32_t *ev = evid ? evid + (size_t)i * m->md.nvars : nullptr;
+        s = m->slice_vars.empty() ? run_program(m, *P, ev, dev, st, !async, nr)
+                                  : run_sliced(m, *P, ev, dev, true, st, nr);
+        if (s) return s;
+        ms += m->last_ms;
+        CK(cudaMemcpyAsync(logz + i, P->d_logz, (size_t)nr * 8, k, st));
+        CK(cudaMemcpyAsync(marg + (size_t)i * P->marg_stride, P->d_marg,
+                           (size_t)nr * P->marg_stride * 8, k, st));
+        if (grad)
+            CK(cudaMemcpyAsync(grad + (size_t)i * P->grad_stride, P->d_grad,
+                               (size_t)nr * P->grad_stride * 8, k, st));
+    }
     if (async) return TN_OK;
     CK(cudaStreamSynchronize(st));
+    m->last_ms = ms;
     if (!dev) {
         for (int b = 0; b < batch; ++b)
             if (!(logz[b] > -INFINITY)) return fail(TN_E_ARG, "p(e) = 0 for evidence set " + std::to_string(b));
@@ -1800,6 +2006,8 @@ tn_status tn_mar_dev(tn_model *m, int batch, const int32_t *evid, const double *
 tn_status tn_map(tn_model *m, const int32_t *evid, const tn_options *opts, int32_t *assign,
                  double *logp) {
     if (!m || !assign || !logp) return fail(TN_E_ARG, "bad argument");
+    if (!m->slice_vars.empty())
+        return fail(TN_E_UNSUPPORTED, "this task does not run on a sliced tree; set the order without slices");
     tn_status s = check_evid(m, 1, evid);
     if (s) return s;
     Program *P;
@@ -1820,6 +2028,8 @@ tn_status tn_map(tn_model *m, const int32_t *evid, const tn_options *opts, int32
 tn_status tn_sample(tn_model *m, const int32_t *evid, uint64_t seed, int64_t n,
                     const tn_options *opts, int8_t *samples) {
     if (!m || n < 0 || (!samples && n)) return fail(TN_E_ARG, "bad argument");
+    if (!m->slice_vars.empty())
+        return fail(TN_E_UNSUPPORTED, "this task does not run on a sliced tree; set the order without slices");
     for (int v = 0; v < m->md.nvars; ++v)
         if (m->md.card[v] > 127) return fail(TN_E_UNSUPPORTED, "domain size above 127");
     tn_status s = check_evid(m, 1, evid);

@@ -438,8 +438,223 @@ static std::vector<int> heuristic_order(const Net &net, bool minfill, std::mt199
     return order;
 }
 
+// ------------------------------------------------------- annealed tree
+//
+// Simulated annealing over contraction trees (local rotations of the binary
+// tree, in the spirit of the tree-annealing order finders the paper cites for
+// its hyper-optimised orders).  A node's labels are computed from two bitsets:
+// U(n), the labels of the leaves under n (bottom-up), and O(n), the labels
+// of every leaf outside n (top-down: O(child) = U(sibling) | O(parent)); then
+// L(n) = U(n) & O(n).  The objective is
+//   log2(sum over nodes of the multiply-add count)  +  w * max(0, sc - target).
+namespace {
+struct SATree {
+    int nl = 0, W = 0;                 // leaves, 64-bit words per bitset
+    std::vector<int> ch0, ch1, par;    // per node id (leaves: -1 children)
+    std::vector<uint64_t> U, O;        // bitsets, node-major
+    std::vector<double> lw;            // log2 card per label
+    std::vector<uint64_t> outbits;
+    int root = -1;
+};
+
+double popw(const uint64_t *b, int W, const std::vector<double> &lw) {
+    double s = 0;
+    for (int w = 0; w < W; ++w) {
+        uint64_t x = b[w];
+        while (x) {
+            int i = __builtin_ctzll(x);
+            s += lw[w * 64 + i];
+            x &= x - 1;
+        }
+    }
+    return s;
+}
+
+// recompute all bitsets; returns (log2 total multiply-adds, sc)
+std::pair<double, double> sa_eval(SATree &T, std::vector<int> &post) {
+    const int W = T.W;
+    int NN = (int)T.ch0.size();
+    // post-order
+    post.clear();
+    std::vector<int> stack{T.root};
+    std::vector<char> seen(NN, 0);
+    while (!stack.empty()) {
+        int v = stack.back();
+        if (v < T.nl || seen[v]) {
+            stack.pop_back();
+            post.push_back(v);
+            continue;
+        }
+        seen[v] = 1;
+        stack.push_back(T.ch1[v]);
+        stack.push_back(T.ch0[v]);
+    }
+    for (int v : post) {
+        if (v < T.nl) continue;
+        uint64_t *u = &T.U[(size_t)v * W];
+        const uint64_t *a = &T.U[(size_t)T.ch0[v] * W], *b = &T.U[(size_t)T.ch1[v] * W];
+        for (int w = 0; w < W; ++w) u[w] = a[w] | b[w];
+    }
+    for (int w = 0; w < W; ++w) T.O[(size_t)T.root * W + w] = T.outbits[w];
+    double maxtc = -1e300, sc = 0;
+    std::vector<double> terms;
+    std::vector<uint64_t> tmp(W), la(W), lb(W);
+    for (int i = (int)post.size() - 1; i >= 0; --i) {
+        int v = post[i];
+        if (v < T.nl) continue;
+        int a = T.ch0[v], b = T.ch1[v];
+        const uint64_t *Ov = &T.O[(size_t)v * W];
+        for (int w = 0; w < W; ++w) {
+            T.O[(size_t)a * W + w] = T.U[(size_t)b * W + w] | Ov[w];
+            T.O[(size_t)b * W + w] = T.U[(size_t)a * W + w] | Ov[w];
+        }
+        for (int w = 0; w < W; ++w) {
+            la[w] = T.U[(size_t)a * W + w] & T.O[(size_t)a * W + w];
+            lb[w] = T.U[(size_t)b * W + w] & T.O[(size_t)b * W + w];
+            tmp[w] = la[w] | lb[w];
+        }
+        double c = popw(tmp.data(), W, T.lw);
+        terms.push_back(c);
+        maxtc = std::max(maxtc, c);
+        for (int w = 0; w < W; ++w) tmp[w] = T.U[(size_t)v * W + w] & Ov[w];
+        sc = std::max(sc, popw(tmp.data(), W, T.lw));
+    }
+    double s = 0;
+    for (double c : terms) s += std::exp2(c - maxtc);
+    return {maxtc + std::log2(s), sc};
+}
+}  // namespace
+
+Tree anneal_tree(const Net &net, const Tree &start, int iters, uint64_t seed, double sc_target) {
+    SATree T;
+    T.nl = (int)net.leaf.size();
+    int L = (int)net.card.size();
+    T.W = (L + 63) / 64;
+    int NN = 2 * T.nl - 1;
+    T.ch0.assign(NN, -1);
+    T.ch1.assign(NN, -1);
+    T.par.assign(NN, -1);
+    for (int i = 0; i < T.nl - 1; ++i) {
+        T.ch0[T.nl + i] = start.left[i];
+        T.ch1[T.nl + i] = start.right[i];
+        T.par[start.left[i]] = T.nl + i;
+        T.par[start.right[i]] = T.nl + i;
+    }
+    T.root = NN - 1;
+    T.U.assign((size_t)NN * T.W, 0);
+    T.O.assign((size_t)NN * T.W, 0);
+    T.lw.assign((size_t)T.W * 64, 0.0);
+    for (int v = 0; v < L; ++v) T.lw[v] = std::log2((double)net.card[v]);
+    T.outbits.assign(T.W, 0);
+    for (int v : net.out) T.outbits[v / 64] |= 1ull << (v % 64);
+    for (int i = 0; i < T.nl; ++i)
+        for (int v : net.leaf[i]) T.U[(size_t)i * T.W + v / 64] |= 1ull << (v % 64);
+    std::vector<int> post;
+    auto obj = [&](std::pair<double, double> r) {
+        return r.first + 4.0 * std::max(0.0, r.second - sc_target);
+    };
+    auto cur = sa_eval(T, post);
+    double fcur = obj(cur);
+    double fbest = fcur;
+    std::vector<int> b0 = T.ch0, b1 = T.ch1, bp = T.par;
+    std::mt19937_64 rng(seed);
+    std::uniform_real_distribution<double> U01(0, 1);
+    std::vector<int> internal;
+    for (int v = T.nl; v < NN; ++v) internal.push_back(v);
+    for (int it = 0; it < iters; ++it) {
+        double beta = 0.5 + 30.0 * it / std::max(1, iters);
+        // rotation at node p whose child c (internal) has children x, y:
+        // p(c(x, y), z) -> p(c(x, z), y)  or  p(c(y, z), x)
+        int p = internal[rng() % internal.size()];
+        int side = rng() & 1;
+        int c = side ? T.ch1[p] : T.ch0[p];
+        if (c < T.nl) continue;
+        int z = side ? T.ch0[p] : T.ch1[p];
+        int pick = rng() & 1;
+        int x = pick ? T.ch1[c] : T.ch0[c];   // stays in c
+        int y = pick ? T.ch0[c] : T.ch1[c];   // moves up to p
+        // apply
+        T.ch0[c] = x;
+        T.ch1[c] = z;
+        T.par[z] = c;
+        if (side) T.ch0[p] = y;
+        else T.ch1[p] = y;
+        T.par[y] = p;
+        auto nxt = sa_eval(T, post);
+        double fn = obj(nxt);
+        if (fn <= fcur || U01(rng) < std::exp(-beta * (fn - fcur))) {
+            fcur = fn;
+            cur = nxt;
+            if (fn < fbest) {
+                fbest = fn;
+                b0 = T.ch0;
+                b1 = T.ch1;
+                bp = T.par;
+            }
+        } else {
+            // undo
+            if (side) T.ch0[p] = z;
+            else T.ch1[p] = z;
+            T.par[z] = p;
+            T.ch0[c] = pick ? y : x;
+            T.ch1[c] = pick ? x : y;
+            T.par[x] = c;
+            T.par[y] = c;
+        }
+    }
+    // renumber the best tree in post-order
+    Tree t;
+    t.nleaves = T.nl;
+    std::vector<int> id(NN, -1);
+    for (int i = 0; i < T.nl; ++i) id[i] = i;
+    std::vector<int> stack{NN - 1};
+    std::vector<char> seen(NN, 0);
+    std::vector<int> order;
+    while (!stack.empty()) {
+        int v = stack.back();
+        if (v < T.nl || seen[v]) {
+            stack.pop_back();
+            if (v >= T.nl) order.push_back(v);
+            continue;
+        }
+        seen[v] = 1;
+        stack.push_back(b1[v]);
+        stack.push_back(b0[v]);
+    }
+    int next = T.nl;
+    for (int v : order) id[v] = next++;
+    t.left.resize(T.nl - 1);
+    t.right.resize(T.nl - 1);
+    for (int v : order) {
+        int k = id[v] - T.nl;
+        t.left[k] = id[b0[v]];
+        t.right[k] = id[b1[v]];
+    }
+    return t;
+}
+
 Tree optimize_tree(const Net &net, int method, int restarts, uint64_t seed) {
     if (method == 0) return greedy_tree(net);
+    if (method == 2) {
+        // anneal from the best heuristic tree, restarts x 20000 rotations,
+        // first towards the smallest space complexity seen, then time
+        Tree t0 = optimize_tree(net, 1, std::max(2, restarts), seed);
+        Plan p0;
+        build_plan(net, t0, p0);
+        Tree best = t0;
+        double bsc = p0.sc_log2, btc = p0.tc_log2;
+        for (int r = 0; r < std::max(1, restarts); ++r) {
+            Tree t = anneal_tree(net, best, 20000, seed + 7919 * (r + 1), bsc - 1.0);
+            Plan p;
+            if (!build_plan(net, t, p).empty()) continue;
+            if (p.sc_log2 < bsc - 1e-9 || (std::fabs(p.sc_log2 - bsc) < 1e-9 && p.tc_log2 < btc)) {
+                best = t;
+                bsc = p.sc_log2;
+                btc = p.tc_log2;
+            }
+        }
+        return best;
+    }
     std::mt19937_64 rng(seed);
     Tree best;
     double bsc = 1e300, btc = 1e300;

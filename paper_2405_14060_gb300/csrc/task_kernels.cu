@@ -24,7 +24,7 @@ __device__ __forceinline__ int exp_bits(unsigned long long b) {
 template <typename T>
 __global__ void k_leaves(const LeafRec *recs, const double *tables, const int *card, int nvars,
                          const int32_t *evid, int nbeta, int log_mode, T *base,
-                         unsigned long long *mx, const int *flags) {
+                         unsigned long long *mx, const int *flags, const int32_t *slice_val) {
     const LeafRec r = recs[blockIdx.x];
     T *dst = base + r.dst;
     __shared__ double smax[32];
@@ -33,7 +33,17 @@ __global__ void k_leaves(const LeafRec *recs, const double *tables, const int *c
         for (int64_t i = threadIdx.x; i < r.size; i += blockDim.x) {
             double x;
             if (r.kind == LEAF_FACTOR) {
-                x = tables[r.src + i];
+                int64_t off = r.src + i;
+                if (r.nkd >= 0) {
+                    off = r.src;
+                    int64_t q = i;
+                    for (int j = r.nkd - 1; j >= 0; --j) {
+                        off += (q % r.ksz[j]) * r.kst[j];
+                        q /= r.ksz[j];
+                    }
+                    for (int j = 0; j < r.nsd; ++j) off += (int64_t)slice_val[r.sidx[j]] * r.sst[j];
+                }
+                x = tables[off];
                 bool in_log = flags && flags[0];
                 if (log_mode && !in_log) x = log(x);
                 else if (!log_mode && in_log) x = exp(x);
@@ -61,6 +71,16 @@ __global__ void k_leaves(const LeafRec *recs, const double *tables, const int *c
     } else {
         int v = r.var, c = card[v];
         int nb = r.beta ? nbeta : 1;
+        if (r.slice_of_var >= 0) {
+            // a sliced variable's vector is the scalar u_v[slice value]
+            int xs = slice_val[r.slice_of_var];
+            for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+                int e = evid ? evid[(int64_t)b * nvars + v] : -1;
+                bool one = e < 0 || e == xs;
+                dst[b] = log_mode ? (one ? T(0) : T(-INFINITY)) : (one ? T(1) : T(0));
+            }
+            c = 1;
+        } else
         for (int64_t t = threadIdx.x; t < (int64_t)nb * c; t += blockDim.x) {
             int b = (int)(t / c), x = (int)(t % c);
             int e = evid ? evid[(int64_t)b * nvars + v] : -1;
@@ -76,10 +96,86 @@ __global__ void k_leaves(const LeafRec *recs, const double *tables, const int *c
 template <typename T>
 void launch_leaves(const LeafRec *recs, int nrec, const double *tables, const int *card,
                    int nvars, const int32_t *evid, int nbeta, int log_mode, T *base,
-                   unsigned long long *mx, const int *flags, cudaStream_t st) {
+                   unsigned long long *mx, const int *flags, const int32_t *slice_val,
+                   cudaStream_t st) {
     if (nrec <= 0) return;
     k_leaves<T><<<nrec, 256, 0, st>>>(recs, tables, card, nvars, evid, nbeta, log_mode, base, mx,
-                                      flags);
+                                      flags, slice_val);
+}
+
+// ------------------------------------------------------------ slicing
+
+__global__ void k_slice_init(int nbeta, int64_t nm, double *M, double *S, double *A) {
+    int b = blockIdx.x;
+    if (threadIdx.x == 0) {
+        M[b] = -INFINITY;
+        S[b] = 0.0;
+    }
+    for (int64_t i = threadIdx.x; i < nm; i += blockDim.x) A[(int64_t)b * nm + i] = 0.0;
+}
+
+void launch_slice_init(int nbeta, int64_t nm, double *M, double *S, double *A, cudaStream_t st) {
+    k_slice_init<<<nbeta, 256, 0, st>>>(nbeta, nm, M, S, A);
+}
+
+__global__ void k_slice_acc(int nbeta, const double *logz, const double *marg, int64_t nm,
+                            const int32_t *slice_val, int nsl, const int32_t *sl_var,
+                            const int64_t *sl_moff, const int32_t *sl_card, double *M, double *S,
+                            double *A) {
+    const int b = blockIdx.x;
+    __shared__ double sh_scale, sh_w;
+    __shared__ int sh_skip;
+    if (threadIdx.x == 0) {
+        double lz = logz[b];
+        sh_skip = !(lz > -INFINITY);
+        if (!sh_skip) {
+            double m = M[b], scale = 1.0;
+            if (!(m > -INFINITY) || lz > m) {
+                scale = m > -INFINITY ? exp(m - lz) : 0.0;
+                M[b] = lz;
+                m = lz;
+            }
+            sh_scale = scale;
+            sh_w = exp(lz - m);
+            S[b] = S[b] * scale + sh_w;
+        }
+    }
+    __syncthreads();
+    if (sh_skip) return;
+    const double scale = sh_scale, w = sh_w;
+    double *a = A + (int64_t)b * nm;
+    if (marg) {
+        const double *p = marg + (int64_t)b * nm;
+        for (int64_t i = threadIdx.x; i < nm; i += blockDim.x) a[i] = a[i] * scale + w * p[i];
+        __syncthreads();
+        for (int j = threadIdx.x; j < nsl; j += blockDim.x)
+            a[sl_moff[j] + slice_val[j]] += w;
+    }
+    (void)sl_var;
+    (void)sl_card;
+}
+
+void launch_slice_acc(int nbeta, const double *logz, const double *marg, int64_t nm,
+                      const int32_t *slice_val, int nsl, const int32_t *sl_var,
+                      const int64_t *sl_moff, const int32_t *sl_card, double *M, double *S,
+                      double *A, cudaStream_t st) {
+    k_slice_acc<<<nbeta, 256, 0, st>>>(nbeta, logz, marg, nm, slice_val, nsl, sl_var, sl_moff,
+                                       sl_card, M, S, A);
+}
+
+__global__ void k_slice_fin(int nbeta, int64_t nm, const double *M, const double *S,
+                            const double *A, double *logz, double *marg) {
+    const int b = blockIdx.x;
+    double s = S[b];
+    if (threadIdx.x == 0) logz[b] = s > 0 ? M[b] + log(s) : -INFINITY;
+    if (marg)
+        for (int64_t i = threadIdx.x; i < nm; i += blockDim.x)
+            marg[(int64_t)b * nm + i] = s > 0 ? A[(int64_t)b * nm + i] / s : NAN;
+}
+
+void launch_slice_fin(int nbeta, int64_t nm, const double *M, const double *S, const double *A,
+                      double *logz, double *marg, cudaStream_t st) {
+    k_slice_fin<<<nbeta, 256, 0, st>>>(nbeta, nm, M, S, A, logz, marg);
 }
 
 // ------------------------------------------------------------------- log Z
@@ -152,6 +248,11 @@ __global__ void k_marginals(const MargRec *recs, int nvars, int nbeta, const T *
     if (t >= (int64_t)nvars * nbeta) return;
     int b = (int)(t / nvars), v = (int)(t % nvars);
     const MargRec r = recs[v];
+    if (r.sliced) {
+        double *o = marg + (int64_t)b * mstride + r.moff;
+        for (int x = 0; x < r.card; ++x) o[x] = 0.0;
+        return;
+    }
     const T *u = fbase + r.fwd + (r.fbeta ? (int64_t)b * r.card : 0);
     const T *ub = abase + r.adj + (r.abeta ? (int64_t)b * r.card : 0);
     double s = 0;
@@ -428,7 +529,7 @@ void launch_cdf_rows(const CDesc &d, int64_t rows, double *cdf, cudaStream_t st)
 #define INST(T)                                                                                  \
     template void launch_leaves<T>(const LeafRec *, int, const double *, const int *, int,      \
                                    const int32_t *, int, int, T *, unsigned long long *,        \
-                                   const int *, cudaStream_t);                                  \
+                                   const int *, const int32_t *, cudaStream_t);                 \
     template void launch_logz<T>(int, const T *, int, const unsigned long long *,              \
                                  const int64_t *, int, double *, double *, int, cudaStream_t);  \
     template void launch_fill_one<T>(T *, int64_t, unsigned long long *, cudaStream_t);         \

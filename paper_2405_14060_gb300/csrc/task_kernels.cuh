@@ -9,22 +9,29 @@ namespace tn {
 
 enum LeafKind { LEAF_FACTOR = 0, LEAF_UNITY = 1, LEAF_EXTERNAL = 2 };
 
+constexpr int LEAF_D = 16;   // scope size of a factor leaf that can be sliced
+
 struct LeafRec {
     int kind;
     int var;              // unity: variable id
     int beta;             // unity: carries the batch label
-    int pad;
+    int slice_of_var;     // unity: index of the variable among the sliced ones, or -1
     int64_t src;          // factor: table offset; external: device address of the data
     int64_t size;         // entries per item
     int64_t dst;          // element offset of the leaf in the arena
     int64_t mx;           // index of its first maximum slot
     const double *sigma;  // external: log2 scale of the data (device), or NULL
+    // factor leaf with sliced labels (nkd >= 0): entry i of the leaf is the
+    // table entry at sum_j digit_j(i) * kst[j] + sum_j slice_val[sidx[j]] * sst[j]
+    int nkd, nsd;
+    int32_t ksz[LEAF_D], sidx[LEAF_D];
+    int64_t kst[LEAF_D], sst[LEAF_D];
 };
 
 struct MargRec {
     int64_t fwd, adj;     // element offsets of u_v and of its adjoint
     int64_t moff;         // offset of variable v's block in a marginal row
-    int card, fbeta, abeta, pad;
+    int card, fbeta, abeta, sliced;   // sliced: marginal filled by the slice combination
 };
 
 struct GradRec {
@@ -35,7 +42,18 @@ struct GradRec {
 template <typename T>
 void launch_leaves(const LeafRec *recs, int nrec, const double *tables, const int *card,
                    int nvars, const int32_t *evid, int nbeta, int log_mode, T *base,
-                   unsigned long long *mx, const int *flags, cudaStream_t st);
+                   unsigned long long *mx, const int *flags, const int32_t *slice_val,
+                   cudaStream_t st);
+// Slice combination (sum over slice assignments, Sec. "Tensor networks":
+// slicing fixes variables; the contraction is the sum over their values):
+// running log-sum-exp of log Z and Z-weighted marginals, per batch item.
+void launch_slice_init(int nbeta, int64_t nm, double *M, double *S, double *A, cudaStream_t st);
+void launch_slice_acc(int nbeta, const double *logz, const double *marg, int64_t nm,
+                      const int32_t *slice_val, int nsl, const int32_t *sl_var,
+                      const int64_t *sl_moff, const int32_t *sl_card, double *M, double *S,
+                      double *A, cudaStream_t st);
+void launch_slice_fin(int nbeta, int64_t nm, const double *M, const double *S, const double *A,
+                      double *logz, double *marg, cudaStream_t st);
 template <typename T>
 void launch_logz(int nbeta, const T *root, int root_beta, const unsigned long long *mx,
                  const int64_t *exps, int nexp, double *logz, double *sigma_out, int maxplus,

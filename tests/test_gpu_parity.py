@@ -287,3 +287,82 @@ def test_autograd_factor_marginals():
         dn[idx] -= eps
         fd = (log_partition(M, up, evt)[0].item() - log_partition(M, dn, evt)[0].item()) / (2 * eps)
         assert abs(fd - g[idx]) < 1e-7
+
+
+def test_workload2_full_size():
+    """24 x 24 grid (the benchmark workload) at full size: log Z against the
+    oracle's FP64 bucket elimination (row-sweep order), and the marginals
+    against central differences of the GPU's own FP64 log Z (a property that
+    holds at any size: d log Z / d h_i = 2 p(s_i = +1) - 1)."""
+    w = synth.workload(2)
+    m = w.model
+    lz_ref = oracle.ve_pr(m, order=np.arange(m.nvars))
+    M = tn.Model.from_synth(m)
+    lz64, marg64 = M.mar(prec="fp64")
+    assert abs(lz64[0] - lz_ref) < 1e-10 * max(1.0, abs(lz_ref)) * 10
+    for prec in ("tf32", "bf16", "fp32"):
+        lz, marg = M.mar(prec=prec)
+        assert abs(lz[0] - lz_ref) <= 1e-4 * abs(lz_ref), prec
+        assert np.max(np.abs(marg - marg64)) < 1e-3, prec
+        assert abs(M.pr(prec=prec)[0] - lz_ref) <= 1e-4 * abs(lz_ref), prec
+    unary = [k for k, sc in enumerate(m.scopes) if len(sc) == 1]
+    eps = 1e-4
+    sp = M.split(marg64[0])
+    for k in unary[::97]:
+        i = int(m.scopes[k][0])
+        t0 = m.tables[k].copy()
+        lzs = []
+        for sgn in (1, -1):
+            m.tables[k] = t0 * np.exp(sgn * eps * np.array([-1.0, 1.0]))
+            lzs.append(tn.Model.from_synth(m).pr(prec="fp64")[0])
+        m.tables[k] = t0
+        fd = (lzs[0] - lzs[1]) / (2 * eps)
+        assert abs(fd - (2 * sp[i][1] - 1)) < 1e-6
+
+
+def test_slicing_pr_mar_matches_oracle():
+    """PR / MAR over a sliced tree (Z-combination over slice assignments)
+    equal the unsliced results and the oracle, with and without evidence on a
+    sliced variable, for a batch of evidence sets."""
+    m = synth.random_markov(12, 16, 3, 13, cards=(2, 3))
+    M = tn.Model.from_synth(m)
+    l, r = M.optimize_order(1, 4, 2)
+    ev = synth.evidence_batch(m, 3, 0.2, 5)
+    ev[1, 4] = 1                       # evidence on a sliced variable
+    M.set_order(l, r, slice_vars=[4, 7])
+    for prec in ("fp64", "fp32"):
+        lz, marg = M.mar(ev, prec=prec)
+        lzp = M.pr(ev, prec=prec)
+        for b in range(ev.shape[0]):
+            lzr, mr = oracle.brute_mar(m, ev[b])
+            tol = 1e-10 if prec == "fp64" else 1e-4 * abs(lzr)
+            assert abs(lz[b] - lzr) <= tol and abs(lzp[b] - lzr) <= tol
+            _marg_close(M, marg[b], mr, 1e-10 if prec == "fp64" else 1e-3)
+    with pytest.raises(tn.TNError):
+        M.map(ev[0])
+
+
+def test_sub_batching_under_budget():
+    """A batch whose program exceeds the HBM budget runs in power-of-two
+    sub-batches with the same results; a budget too small for one evidence
+    set is TN_E_OOM."""
+    m = synth.random_markov(12, 16, 3, 17, cards=(2, 3))
+    ev = synth.evidence_batch(m, 13, 0.2, 3)
+    ref_lz, ref_m = tn.Model.from_synth(m).mar(ev, prec="fp64")
+    with pytest.raises(tn.TNError) as e:
+        tn.Model.from_synth(m).mar(ev[:1], prec="fp64", budget=64)
+    assert e.value.status == 4
+    # smallest power-of-two budget that holds one evidence set
+    b = 1024
+    while True:
+        try:
+            tn.Model.from_synth(m).mar(ev[:1], prec="fp64", budget=b)
+            break
+        except tn.TNError:
+            b *= 2
+    M = tn.Model.from_synth(m)
+    lz, mg = M.mar(ev, prec="fp64", budget=3 * b)
+    np.testing.assert_allclose(lz, ref_lz, rtol=0, atol=1e-10)
+    np.testing.assert_allclose(mg, ref_m, rtol=0, atol=1e-10)
+    lzp = tn.Model.from_synth(m).pr(ev, prec="fp32", budget=3 * b)
+    np.testing.assert_allclose(lzp, ref_lz, rtol=1e-4)
