@@ -614,6 +614,32 @@ static bool make_absorb(const std::vector<int> &card, const Labels &lx, bool bx,
         raw.push_back({card[v], stride_in(card, lx, v), stride_in(card, ly, v),
                        sin_or0(card, lw, sw, v)});
     auto f = fuse3(raw);
+    // inner dims: the fastest dims, at most 2048 positions (a dim that would
+    // overflow that is split into (outer part, inner part)); their offset
+    // table (12 bytes a position) stays under the 48 KB shared-memory default
+    int ninner = 0;
+    {
+        int64_t nin = 1;
+        int k = (int)f.size() - 1;
+        while (k >= 0) {
+            if (nin * f[k].sz <= 2048) {
+                nin *= f[k].sz;
+                ++ninner;
+                --k;
+                continue;
+            }
+            int64_t lo = 2048 / nin;
+            while (lo > 1 && f[k].sz % lo) --lo;
+            if (lo >= 2) {
+                SDim hi{f[k].sz / lo, f[k].s0 * lo, f[k].s1 * lo, f[k].s2 * lo};
+                SDim lw2{lo, f[k].s0, f[k].s1, f[k].s2};
+                f[k] = hi;
+                f.insert(f.begin() + k + 1, lw2);
+                ++ninner;
+            }
+            break;
+        }
+    }
     if ((int)f.size() > MAXD) return false;
     d.nrd = (int)f.size();
     d.nr = 1;
@@ -632,19 +658,17 @@ static bool make_absorb(const std::vector<int> &card, const Labels &lx, bool bx,
         d.rsh[i] = sh;
         if (p2) sh += __builtin_ctzll((unsigned long long)f[i].sz);
     }
-    // inner dims: the fastest dims up to >= 1024 positions, offsets in 32 bits
+    // inner offsets (shared-memory table) must fit 32 bits
     d.nin = 1;
-    d.nin_d = 0;
+    d.nin_d = ninner;
     int64_t ex = 0, ey = 0, ew = 0;
-    for (int i = d.nrd - 1; i >= 0 && d.nin < 1024; --i) {
+    for (int i = d.nrd - 1; i >= d.nrd - ninner; --i) {
         ex += (f[i].sz - 1) * f[i].s0;
         ey += (f[i].sz - 1) * f[i].s1;
         ew += (f[i].sz - 1) * f[i].s2;
-        if (ex >= (1LL << 31) || ey >= (1LL << 31) || ew >= (1LL << 31)) break;
         d.nin *= f[i].sz;
-        d.nin_d++;
     }
-    if (d.nin_d == 0 && d.nrd > 0) return false;
+    if (ex >= (1LL << 31) || ey >= (1LL << 31) || ew >= (1LL << 31)) return false;
     d.nouter = d.nr / d.nin;
     d.nbeta = by ? nbeta : 1;
     d.bsx = (by && bx) ? perx : 0;
@@ -689,6 +713,30 @@ static bool make_reduce(const std::vector<int> &card, const Labels &lx, bool bx,
     for (int v : G) g.push_back({card[v], stride_in(card, lx, v), stride_in(card, lz, v), stride_in(card, lo, v)});
     for (int v : M) m.push_back({card[v], sin_or0(card, lx, sx, v), sin_or0(card, lz, sz, v), 0});
     auto fg = fuse3(g), fm = fuse3(m);
+    // inner summed dims (offset table of at most 2048 positions)
+    int ninner = 0;
+    {
+        int64_t nin = 1;
+        int k = (int)fm.size() - 1;
+        while (k >= 0) {
+            if (nin * fm[k].sz <= 2048) {
+                nin *= fm[k].sz;
+                ++ninner;
+                --k;
+                continue;
+            }
+            int64_t lo = 2048 / nin;
+            while (lo > 1 && fm[k].sz % lo) --lo;
+            if (lo >= 2) {
+                SDim hi{fm[k].sz / lo, fm[k].s0 * lo, fm[k].s1 * lo, 0};
+                SDim lw2{lo, fm[k].s0, fm[k].s1, 0};
+                fm[k] = hi;
+                fm.insert(fm.begin() + k + 1, lw2);
+                ++ninner;
+            }
+            break;
+        }
+    }
     if ((int)fg.size() > MAXD || (int)fm.size() > MAXD) return false;
     d.ngd = (int)fg.size();
     d.ng = 1;
@@ -715,6 +763,16 @@ static bool make_reduce(const std::vector<int> &card, const Labels &lx, bool bx,
         d.msh[i] = sh;
         if (p2) sh += __builtin_ctzll((unsigned long long)fm[i].sz);
     }
+    d.nin_d = ninner;
+    d.nin = 1;
+    int64_t ex = 0, ez = 0;
+    for (int i = d.nmd - 1; i >= d.nmd - ninner; --i) {
+        ex += (fm[i].sz - 1) * fm[i].s0;
+        ez += (fm[i].sz - 1) * fm[i].s1;
+        d.nin *= fm[i].sz;
+    }
+    if (ex >= (1LL << 31) || ez >= (1LL << 31)) return false;
+    d.nouter = d.nm / d.nin;
     d.nbeta = bo ? nbeta : 1;
     d.bsx = (bo && bx) ? perx : 0;
     d.bsz = (bo && bz) ? perz : 0;
@@ -765,6 +823,41 @@ static bool to_micro(const CDesc &d, const char *arena, int esz, const unsigned 
     m.mxb_bs = d.mxb_bs;
     m.amoff = d.argmax ? d.argmax - amb : -1;
     return true;
+}
+
+// Inner offset tables of the streaming kernels (computed once per node).
+static void absorb_table(const ADesc &d, std::vector<int32_t> &out) {
+    const int nin = (int)d.nin, nod = d.nrd - d.nin_d;
+    out.assign((size_t)3 * nin, 0);
+    for (int i = 0; i < nin; ++i) {
+        int64_t r = i, x0 = 0, y0 = 0, w0 = 0;
+        for (int k = d.nrd - 1; k >= nod; --k) {
+            int64_t dg = r % d.rsz[k];
+            r /= d.rsz[k];
+            x0 += dg * d.rsx[k];
+            y0 += dg * d.rsy[k];
+            w0 += dg * d.rsw[k];
+        }
+        out[i] = (int32_t)x0;
+        out[nin + i] = (int32_t)y0;
+        out[2 * nin + i] = (int32_t)w0;
+    }
+}
+
+static void reduce_table(const RDesc &d, std::vector<int32_t> &out) {
+    const int nin = (int)d.nin, nod = d.nmd - d.nin_d;
+    out.assign((size_t)2 * nin, 0);
+    for (int i = 0; i < nin; ++i) {
+        int64_t r = i, x0 = 0, z0 = 0;
+        for (int k = d.nmd - 1; k >= nod; --k) {
+            int64_t dg = r % d.msz[k];
+            r /= d.msz[k];
+            x0 += dg * d.msx[k];
+            z0 += dg * d.msz2[k];
+        }
+        out[i] = (int32_t)x0;
+        out[nin + i] = (int32_t)z0;
+    }
 }
 
 // Build (plan, allocate, describe, capture) a program.
@@ -1200,6 +1293,28 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
         CK(cudaMemcpy(P.d_mb, P.mb.data(), sizeof(MicroDesc) * P.mb.size(), cudaMemcpyHostToDevice));
         CK(P.mem.alloc(&P.d_mb_beg, 4 * P.mb_beg.size()));
         CK(cudaMemcpy(P.d_mb_beg, P.mb_beg.data(), 4 * P.mb_beg.size(), cudaMemcpyHostToDevice));
+    }
+    // inner offset tables of the streaming steps, one device buffer
+    {
+        std::vector<int32_t> all, t;
+        std::vector<std::pair<Step *, size_t>> where;
+        for (auto *steps : {&P.fsteps, &P.bsteps})
+            for (auto &st : *steps) {
+                if (st.kind == 2) absorb_table(st.ad, t);
+                else if (st.kind == 3) reduce_table(st.rd, t);
+                else continue;
+                where.push_back({&st, all.size()});
+                all.insert(all.end(), t.begin(), t.end());
+            }
+        if (!all.empty()) {
+            int32_t *dt = nullptr;
+            CK(P.mem.alloc(&dt, all.size() * 4));
+            CK(cudaMemcpy(dt, all.data(), all.size() * 4, cudaMemcpyHostToDevice));
+            for (auto &w : where) {
+                if (w.first->kind == 2) w.first->ad.tab = dt + w.second;
+                else w.first->rd.tab = dt + w.second;
+            }
+        }
     }
     // GEMM workspaces, then patch the steps' workspace pointers
     if (need_x) CK(P.mem.alloc(&P.wsX, need_x));

@@ -31,6 +31,7 @@ struct ADesc {
     int mxx_bs, mxw_bs;
     unsigned long long *mxy;
     int32_t *argmax;                  // max-plus: flat summed index per output
+    const int32_t *tab;               // inner offsets: X [nin], Y [nin], W [nin] (device)
 };
 
 // Reduce: O[g, s, t] = sum_m X[g, m, s] Z[g, m, t]
@@ -39,6 +40,8 @@ struct ADesc {
 //   s: labels of X kept in O, t: labels of Z kept in O  (ns * nt <= 64)
 struct RDesc {
     int ngd, nmd, pow2m;
+    int nin_d;                        // the last nin_d summed dims are "inner" (offset table)
+    int64_t nin, nouter;
     int32_t gsz[MAXD];
     int64_t gsx[MAXD], gsz2[MAXD], gso[MAXD];
     int32_t msz[MAXD], msh[MAXD];
@@ -54,6 +57,7 @@ struct RDesc {
     const unsigned long long *mxx, *mxz;
     int mxx_bs, mxz_bs;
     unsigned long long *mxo;
+    const int32_t *tab;               // inner offsets: X [nin], Z [nin] (device)
 };
 
 template <typename T>

@@ -23,19 +23,19 @@
 
 namespace tn {
 
-// Positions are processed in tiles of TILE consecutive inner positions of one
-// outer position: the outer offsets are decoded once per tile (64-bit), the
-// inner ones per position in 32-bit arithmetic, and every thread issues the
-// loads of TILE / blockDim positions before using them.
-constexpr int A_TILE = 1024;
+// Inner positions (the fastest dims, at most A_INNER entries) get their offsets
+// from a table computed on the host when the node is planned (device memory,
+// read through L1); each outer index is decoded once for its whole inner
+// slice.  A position then costs one cached table load per operand plus its
+// data accesses.
+constexpr int A_INNER = 2048;
 
-// NS / NT are the exact numbers of summed / new combinations.  Sum-product
-// accumulates the unscaled products and applies the operands' power-of-two
-// scale factors once per output (stored tensors are kept near 1 by the
-// rescaling, so the unscaled products stay in range).
 template <typename T, int NS, int NT, int SEMI>
 __global__ void __launch_bounds__(256) k_absorb(const __grid_constant__ ADesc d) {
-    constexpr int U = NS * NT <= 16 ? 4 : NS * NT <= 64 ? 2 : 1;
+    constexpr int U = NS * NT <= 4 ? 8 : NS * NT <= 16 ? 4 : NS * NT <= 64 ? 2 : 1;
+    const int nin = (int)d.nin;
+    const int *tx = d.tab, *ty = d.tab + nin, *tw = d.tab + 2 * nin;
+    const int nod = d.nrd - d.nin_d;
     const int64_t beta = blockIdx.y;
     T mx = 0;
     T scale = T(1);
@@ -44,98 +44,75 @@ __global__ void __launch_bounds__(256) k_absorb(const __grid_constant__ ADesc d)
         T sw = d.mxw ? pow2neg<T>(exp_of_bits(d.mxw[beta * d.mxw_bs])) : T(1);
         scale = sx * sw;
     }
-    const int nod = d.nrd - d.nin_d;
-    const int64_t ctiles = (d.nin + A_TILE - 1) / A_TILE;
-    const int64_t ntiles = d.nouter * ctiles;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t o = tile / ctiles, c = tile - o * ctiles;
+    for (int64_t o = blockIdx.x; o < d.nouter; o += gridDim.x) {
         int64_t bx = beta * d.bsx, by = beta * d.bsy, bw = beta * d.bsw;
         {
             int64_t r = o;
-            for (int i = nod - 1; i >= 0; --i) {
-                int64_t dg = r % d.rsz[i];
-                r /= d.rsz[i];
-                bx += dg * d.rsx[i];
-                by += dg * d.rsy[i];
-                bw += dg * d.rsw[i];
+            for (int k = nod - 1; k >= 0; --k) {
+                int64_t dg = r % d.rsz[k];
+                r /= d.rsz[k];
+                bx += dg * d.rsx[k];
+                by += dg * d.rsy[k];
+                bw += dg * d.rsw[k];
             }
-        }
-      for (int sub = 0; sub < A_TILE / (256 * U); ++sub) {
-        int ox[U], oy[U], ow[U];
-        bool on[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            int ii = (int)(c * A_TILE) + sub * 256 * U + threadIdx.x + u * 256;
-            on[u] = ii < d.nin;
-            int r = on[u] ? ii : 0, x0 = 0, y0 = 0, w0 = 0;
-            if (d.pow2r) {
-                for (int i = nod; i < d.nrd; ++i) {
-                    int dg = (r >> d.rsh[i]) & (d.rsz[i] - 1);
-                    x0 += dg * (int)d.rsx[i];
-                    y0 += dg * (int)d.rsy[i];
-                    w0 += dg * (int)d.rsw[i];
-                }
-            } else {
-                for (int i = d.nrd - 1; i >= nod; --i) {
-                    int dg = r % d.rsz[i];
-                    r /= d.rsz[i];
-                    x0 += dg * (int)d.rsx[i];
-                    y0 += dg * (int)d.rsy[i];
-                    w0 += dg * (int)d.rsw[i];
-                }
-            }
-            ox[u] = x0;
-            oy[u] = y0;
-            ow[u] = w0;
         }
         const T *Xb = (const T *)d.X + bx;
         const T *Wb = (const T *)d.W + bw;
         T *Yb = (T *)d.Y + by;
-        T x[U][NS];
+        for (int j0 = threadIdx.x; j0 < nin; j0 += 256 * U) {
+            T x[U][NS];
+            int oy[U], ow[U];
+            bool on[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u)
+            for (int u = 0; u < U; ++u) {
+                int j = j0 + u * 256;
+                on[u] = j < nin;
+                int jj = on[u] ? j : 0;
+                int ox = __ldg(tx + jj);
+                oy[u] = __ldg(ty + jj);
+                ow[u] = __ldg(tw + jj);
 #pragma unroll
-            for (int s = 0; s < NS; ++s)
-                x[u][s] = (on[u] && s < d.ns) ? Xb[ox[u] + d.xoff[s]] : T(0);
+                for (int s = 0; s < NS; ++s)
+                    x[u][s] = (on[u] && (NS == 1 || s < d.ns)) ? Xb[ox + d.xoff[s]] : T(0);
+            }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            if (!on[u]) continue;
-            const T *W = Wb + ow[u];
-            T *Y = Yb + oy[u];
+            for (int u = 0; u < U; ++u) {
+                if (!on[u]) continue;
+                const T *W = Wb + ow[u];
+                T *Y = Yb + oy[u];
 #pragma unroll
-            for (int t = 0; t < NT; ++t) {
-                if (NT > 1 && t >= d.nt) break;
-                if (SEMI == SUM) {
-                    T acc = 0;
+                for (int t = 0; t < NT; ++t) {
+                    if (NT > 1 && t >= d.nt) break;
+                    if (SEMI == SUM) {
+                        T acc = 0;
 #pragma unroll
-                    for (int s = 0; s < NS; ++s)
-                        if (NS == 1 || s < d.ns) acc += x[u][s] * __ldg(W + d.wso[s] + d.wto[t]);
-                    Y[d.yoff[t]] = acc * scale;
-                    mx = mx > acc ? mx : acc;
-                } else {
-                    T best = -INFINITY;
-                    int32_t bk = 0;
+                        for (int s = 0; s < NS; ++s)
+                            if (NS == 1 || s < d.ns) acc += x[u][s] * __ldg(W + d.wso[s] + d.wto[t]);
+                        Y[d.yoff[t]] = acc * scale;
+                        mx = mx > acc ? mx : acc;
+                    } else {
+                        T best = -INFINITY;
+                        int32_t bk = 0;
 #pragma unroll
-                    for (int s = 0; s < NS; ++s) {
-                        if (NS > 1 && s >= d.ns) break;
-                        T v = x[u][s] + __ldg(W + d.wso[s] + d.wto[t]);
-                        if (v > best) { best = v; bk = s; }
+                        for (int s = 0; s < NS; ++s) {
+                            if (NS > 1 && s >= d.ns) break;
+                            T v = x[u][s] + __ldg(W + d.wso[s] + d.wto[t]);
+                            if (v > best) { best = v; bk = s; }
+                        }
+                        Y[d.yoff[t]] = best;
+                        if (d.argmax) d.argmax[by + oy[u] + d.yoff[t]] = bk;
                     }
-                    Y[d.yoff[t]] = best;
-                    if (d.argmax) d.argmax[by + oy[u] + d.yoff[t]] = bk;
                 }
             }
         }
-      }
     }
     if (SEMI == SUM && d.mxy) block_max_atomic(d.mxy + beta, (double)mx * (double)scale);
 }
 
 template <typename T, int NS, int NT>
 static void absorb_go(const ADesc &d, int semiring, cudaStream_t st) {
-    int64_t tiles = d.nouter * ((d.nin + A_TILE - 1) / A_TILE);
     int64_t cap = std::max<int64_t>(1, (152LL * 16) / std::max(1, d.nbeta));
-    dim3 grid((unsigned)std::max<int64_t>(1, std::min(tiles, cap)), (unsigned)d.nbeta, 1);
+    dim3 grid((unsigned)std::max<int64_t>(1, std::min(d.nouter, cap)), (unsigned)d.nbeta, 1);
     if (semiring == SUM) k_absorb<T, NS, NT, SUM><<<grid, 256, 0, st>>>(d);
     else k_absorb<T, NS, NT, MAXPLUS><<<grid, 256, 0, st>>>(d);
 }
@@ -192,16 +169,20 @@ __device__ __forceinline__ void group_offsets(const RDesc &d, int64_t gi, int64_
     }
 }
 
+// The summed positions m split into inner ones (offset table computed at plan
+// time, at most A_INNER) and outer ones; blocks take contiguous ranges of
+// (outer index, inner chunk) tiles of one group.
 template <typename T, int NS, int NT>
 __global__ void __launch_bounds__(256) k_reduce_part(const __grid_constant__ RDesc d,
                                                      int64_t chunk, int nchunks, T *part) {
+    const int nin = (int)d.nin;
+    const int *tx = d.tab, *tz = d.tab + nin;
+    const int nod = d.nmd - d.nin_d;
     int64_t g = (int64_t)blockIdx.y + (int64_t)gridDim.y * blockIdx.z;
     if (g >= d.ng * d.nbeta) return;
     int64_t beta = g / d.ng, gi = g - beta * d.ng;
-    int64_t ox = beta * d.bsx, oz = beta * d.bsz, oo = 0;
-    group_offsets(d, gi, ox, oz, oo);
-    const T *X = (const T *)d.X + ox;
-    const T *Z = (const T *)d.Z + oz;
+    int64_t gx = beta * d.bsx, gz = beta * d.bsz, go = 0;
+    group_offsets(d, gi, gx, gz, go);
     T sx = d.mxx ? pow2neg<T>(exp_of_bits(d.mxx[beta * d.mxx_bs])) : T(1);
     T sz = d.mxz ? pow2neg<T>(exp_of_bits(d.mxz[beta * d.mxz_bs])) : T(1);
     T acc[NS][NT];
@@ -209,42 +190,49 @@ __global__ void __launch_bounds__(256) k_reduce_part(const __grid_constant__ RDe
     for (int s = 0; s < NS; ++s)
 #pragma unroll
         for (int t = 0; t < NT; ++t) acc[s][t] = 0;
-    int64_t m0 = (int64_t)blockIdx.x * chunk, m1 = min(m0 + chunk, d.nm);
-    constexpr int U = NS * NT <= 4 ? 4 : NS * NT <= 16 ? 2 : 1;
-    for (int64_t mb = m0 + threadIdx.x; mb < m1; mb += (int64_t)blockDim.x * U) {
-        T x[U][NS], z[U][NT];
+    // tiles: (outer index, inner chunk of 1024)
+    const int64_t cper = (nin + 1023) / 1024;
+    const int64_t ntile = d.nouter * cper;
+    const int64_t t0 = (int64_t)blockIdx.x * chunk, t1 = min(t0 + chunk, ntile);
+    constexpr int U = NS * NT <= 4 ? 8 : NS * NT <= 16 ? 4 : NS * NT <= 32 ? 2 : 1;
+    for (int64_t tile = t0; tile < t1; ++tile) {
+        int64_t o = tile / cper;
+        int c = (int)(tile - o * cper);
+        int64_t bx = gx, bz = gz;
+        {
+            int64_t r = o;
+            for (int k = nod - 1; k >= 0; --k) {
+                int64_t dg = r % d.msz[k];
+                r /= d.msz[k];
+                bx += dg * d.msx[k];
+                bz += dg * d.msz2[k];
+            }
+        }
+        const T *X = (const T *)d.X + bx;
+        const T *Z = (const T *)d.Z + bz;
+        const int jend = min(nin, (c + 1) * 1024);
+        for (int j0 = c * 1024 + threadIdx.x; j0 < jend; j0 += 256 * U) {
+            T x[U][NS], z[U][NT];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            int64_t m = mb + (int64_t)u * blockDim.x;
-            bool on = m < m1;
-            int64_t mxo = 0, mzo = 0;
-            if (d.pow2m) {
-#pragma unroll 4
-                for (int i = 0; i < d.nmd; ++i) {
-                    int64_t dg = (m >> d.msh[i]) & (int64_t)(d.msz[i] - 1);
-                    mxo += dg * d.msx[i];
-                    mzo += dg * d.msz2[i];
-                }
-            } else {
-                int64_t r = m;
-                for (int i = d.nmd - 1; i >= 0; --i) {
-                    int64_t dg = r % d.msz[i];
-                    r /= d.msz[i];
-                    mxo += dg * d.msx[i];
-                    mzo += dg * d.msz2[i];
-                }
+            for (int u = 0; u < U; ++u) {
+                int j = j0 + u * 256;
+                bool on = j < jend;
+                int jj = on ? j : 0;
+                int ox = __ldg(tx + jj), oz = __ldg(tz + jj);
+#pragma unroll
+                for (int s = 0; s < NS; ++s)
+                    x[u][s] = (on && (NS == 1 || s < d.ns)) ? X[ox + d.xoff[s]] : T(0);
+#pragma unroll
+                for (int t = 0; t < NT; ++t)
+                    z[u][t] = (on && (NT == 1 || t < d.nt)) ? Z[oz + d.zoff[t]] : T(0);
             }
 #pragma unroll
-            for (int s = 0; s < NS; ++s) x[u][s] = (on && s < d.ns) ? X[mxo + d.xoff[s]] : T(0);
+            for (int u = 0; u < U; ++u)
 #pragma unroll
-            for (int t = 0; t < NT; ++t) z[u][t] = (on && t < d.nt) ? Z[mzo + d.zoff[t]] : T(0);
+                for (int s = 0; s < NS; ++s)
+#pragma unroll
+                    for (int t = 0; t < NT; ++t) acc[s][t] += x[u][s] * z[u][t];
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-#pragma unroll
-            for (int s = 0; s < NS; ++s)
-#pragma unroll
-                for (int t = 0; t < NT; ++t) acc[s][t] += (x[u][s] * sx) * (z[u][t] * sz);
     }
     __shared__ T red[8][NS * NT];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -261,7 +249,7 @@ __global__ void __launch_bounds__(256) k_reduce_part(const __grid_constant__ RDe
     for (int i = threadIdx.x; i < NS * NT; i += blockDim.x) {
         T v = 0;
         for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += red[q][i];
-        part[(g * nchunks + blockIdx.x) * (NS * NT) + i] = v;
+        part[(g * nchunks + blockIdx.x) * (8 * 8) + i] = v * (sx * sz);
     }
 }
 
@@ -280,7 +268,7 @@ __global__ void __launch_bounds__(256) k_reduce_fin(const __grid_constant__ RDes
         beta = g / d.ng;
         if (s < d.ns && t < d.nt) {
             T acc = 0;
-            for (int c = 0; c < nchunks; ++c) acc += part[(g * nchunks + c) * (NS * NT) + i];
+            for (int c = 0; c < nchunks; ++c) acc += part[(g * nchunks + c) * (8 * 8) + i];
             int64_t ox = 0, oz = 0, oo = beta * d.bso;
             group_offsets(d, g - beta * d.ng, ox, oz, oo);
             ((T *)d.O)[oo + d.oso[s] + d.oto[t]] = acc;
@@ -294,14 +282,10 @@ __global__ void __launch_bounds__(256) k_reduce_fin(const __grid_constant__ RDes
 
 static void reduce_shape(const RDesc &d, int64_t &chunk, int &nchunks) {
     int64_t groups = d.ng * d.nbeta;
+    int64_t ntile = d.nouter * ((d.nin + 1023) / 1024);
     int64_t want = std::max<int64_t>(1, (152LL * 8) / std::max<int64_t>(1, groups));
-    chunk = std::max<int64_t>(2048, (d.nm + want - 1) / want);
-    nchunks = (int)((d.nm + chunk - 1) / chunk);
-}
-
-static int reduce_tile(const RDesc &d) {
-    int m = std::min(8, d.ns > d.nt ? d.ns : d.nt);
-    return m <= 1 ? 1 : m <= 2 ? 2 : m <= 4 ? 4 : 8;
+    chunk = std::max<int64_t>(1, (ntile + want - 1) / want);
+    nchunks = (int)((ntile + chunk - 1) / chunk);
 }
 
 #ifdef TN_STREAM_HOST_DEFS
@@ -309,12 +293,11 @@ size_t reduce_scratch_bytes(const RDesc &d, int elem_bytes) {
     int64_t chunk;
     int nchunks;
     reduce_shape(d, chunk, nchunks);
-    int q = 8;
-    return (size_t)(d.ng * d.nbeta * nchunks * q * q) * elem_bytes;
+    return (size_t)(d.ng * d.nbeta * nchunks * 64) * elem_bytes;
 }
 #endif
 
-template <typename T, int Q>
+template <typename T, int NS, int NT>
 static void reduce_go(const RDesc &d, void *scratch, cudaStream_t st) {
     int64_t chunk;
     int nchunks;
@@ -322,20 +305,26 @@ static void reduce_go(const RDesc &d, void *scratch, cudaStream_t st) {
     int64_t groups = d.ng * d.nbeta;
     dim3 grid((unsigned)nchunks, (unsigned)std::min<int64_t>(groups, 65535),
               (unsigned)((groups + 65534) / 65535));
-    k_reduce_part<T, Q, Q><<<grid, 256, 0, st>>>(d, chunk, nchunks, (T *)scratch);
-    int64_t tot = groups * Q * Q;
-    k_reduce_fin<T, Q, Q><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(d, nchunks,
-                                                                         (const T *)scratch);
+    k_reduce_part<T, NS, NT><<<grid, 256, 0, st>>>(d, chunk, nchunks, (T *)scratch);
+    int64_t tot = groups * NS * NT;
+    k_reduce_fin<T, NS, NT><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(d, nchunks,
+                                                                           (const T *)scratch);
+}
+
+template <typename T, int NS>
+static void reduce_nt(const RDesc &d, void *scratch, cudaStream_t st) {
+    if (d.nt <= 1) reduce_go<T, NS, 1>(d, scratch, st);
+    else if (d.nt <= 2) reduce_go<T, NS, 2>(d, scratch, st);
+    else if (d.nt <= 4) reduce_go<T, NS, 4>(d, scratch, st);
+    else reduce_go<T, NS, 8>(d, scratch, st);
 }
 
 template <typename T>
 static void reduce_one(const RDesc &d, void *scratch, cudaStream_t st) {
-    switch (reduce_tile(d)) {
-        case 1: reduce_go<T, 1>(d, scratch, st); break;
-        case 2: reduce_go<T, 2>(d, scratch, st); break;
-        case 4: reduce_go<T, 4>(d, scratch, st); break;
-        default: reduce_go<T, 8>(d, scratch, st); break;
-    }
+    if (d.ns <= 1) reduce_nt<T, 1>(d, scratch, st);
+    else if (d.ns <= 2) reduce_nt<T, 2>(d, scratch, st);
+    else if (d.ns <= 4) reduce_nt<T, 4>(d, scratch, st);
+    else reduce_nt<T, 8>(d, scratch, st);
 }
 
 // Outputs with more than 8 x 8 (s, t) combinations run as several launches

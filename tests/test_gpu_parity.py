@@ -366,3 +366,55 @@ def test_sub_batching_under_budget():
     np.testing.assert_allclose(mg, ref_m, rtol=0, atol=1e-10)
     lzp = tn.Model.from_synth(m).pr(ev, prec="fp32", budget=3 * b)
     np.testing.assert_allclose(lzp, ref_lz, rtol=1e-4)
+
+
+def test_workload4_batched_slice():
+    """Workload 4 (3-regular, 200 spins, evidence sets with 10% observed) on
+    its annealed tree: a batch of 16 evidence sets in BF16 and FP64 against
+    the oracle's bucket elimination for two of them, and the batch against
+    single-set runs."""
+    w = synth.workload(4)
+    m, ev = w.model, w.evid[:16]
+    M = tn.Model.from_synth(m)
+    M.set_order(*M.optimize_order(2, 6, 1))
+    lz64, mg64 = M.mar(ev, prec="fp64")
+    for b in (0, 9):
+        assert abs(lz64[b] - oracle.ve_pr(m, ev[b])) < 1e-9
+    lz1, mg1 = M.mar(ev[9:10], prec="fp64")
+    assert abs(lz1[0] - lz64[9]) < 1e-9
+    np.testing.assert_allclose(mg1[0], mg64[9], atol=1e-10)
+    for prec in ("bf16", "tf32"):
+        lz, mg = M.mar(ev, prec=prec)
+        np.testing.assert_allclose(lz, lz64, rtol=1e-4)
+        assert np.max(np.abs(mg - mg64)) < 1e-3
+    # observed variables get the indicator of their value
+    row = M.split(mg64[0])
+    for v in np.nonzero(ev[0] >= 0)[0]:
+        assert row[v][ev[0][v]] == 1.0
+
+
+def test_rrg3_sampling_statistics():
+    """Backward sampling on a random 3-regular graph: per-spin frequencies
+    within 5 sigma of the oracle's marginals and edge correlations
+    E[s_i s_j] within 5 sigma of the exact ones (from brute force)."""
+    m = synth.rrg3_ising(16, 31, field=True)
+    M = tn.Model.from_synth(m)
+    M.set_order(*M.optimize_order(1, 4, 2))
+    n = 100000
+    s = M.sample(n, seed=11, prec="fp32")
+    _, marg = oracle.ve_mar(m)
+    p1 = np.array([mv[1] for mv in marg])
+    emp = s.mean(axis=0)
+    sig = np.sqrt(p1 * (1 - p1) / n) + 1e-12
+    assert np.all(np.abs(emp - p1) < 5 * sig + 1e-4)
+    joint = oracle.brute_joint(m)
+    X = ((np.arange(len(joint))[:, None] >> np.arange(m.nvars)[::-1]) & 1)
+    S = 2 * X - 1
+    Ss = 2 * s.astype(np.int64) - 1
+    for sc in m.scopes:
+        if len(sc) != 2:
+            continue
+        i, j = int(sc[0]), int(sc[1])
+        exact = np.sum(joint * S[:, i] * S[:, j])
+        empc = np.mean(Ss[:, i] * Ss[:, j])
+        assert abs(empc - exact) < 5 * np.sqrt(max(1e-12, 1 - exact ** 2) / n) + 1e-4
