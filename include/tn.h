@@ -138,6 +138,21 @@ tn_status tn_tree_from_elimination(const tn_model *m, int nelim, const int *orde
 tn_status tn_optimize_order(const tn_model *m, int method, int restarts, uint64_t seed,
                             int *left, int *right);
 
+/* Equivalent tree with runs of absorption steps re-associated.  The
+ * contraction is associative (Sec. Tensor networks: every binary tree gives
+ * the same result; only the cost changes), so a run of steps in which a large
+ * tensor absorbs small ones one at a time, Y_i = con(Y_(i-1), W_i), is
+ * rewritten as V = con(W_1, ..., W_k) followed by one step Y_k = con(Y_0, V):
+ * the large tensor is read and written once per run instead of once per
+ * step.  Runs are chosen per chain by dynamic programming over a time model
+ * of the streaming kernels (bytes, FLOPs, a fixed cost per launch).  Input:
+ * a tree in tn_set_order's form (nleaves-1 entries each); output: the new
+ * tree, post-ordered, in left_out/right_out (nleaves-1 entries each; may
+ * alias neither input).  Host only.  TN_E_ORDER if the input is not a valid
+ * tree.  The result is unchanged where no run pays off. */
+tn_status tn_reassociate(const tn_model *m, const int *left, const int *right,
+                         int *left_out, int *right_out);
+
 /* Complexities of the current tree for `batch` evidence sets:
  * out[0] = log2 of the total multiply-add count (time complexity, paper:
  * product over the union of the labels of each pairwise contraction),

@@ -670,6 +670,16 @@ static bool make_absorb(const std::vector<int> &card, const Labels &lx, bool bx,
     }
     if (ex >= (1LL << 31) || ey >= (1LL << 31) || ew >= (1LL << 31)) return false;
     d.nouter = d.nr / d.nin;
+    // shared-label combinations (R dims that W holds), mixed radix, last fastest
+    {
+        int64_t c = 1;
+        for (int i = d.nrd - 1; i >= 0; --i) {
+            d.rshc[i] = f[i].s2 ? (int32_t)c : 0;
+            if (f[i].s2) c *= f[i].sz;
+            if (c >= (1LL << 30)) return false;
+        }
+        d.nsh = (int)c;
+    }
     d.nbeta = by ? nbeta : 1;
     d.bsx = (by && bx) ? perx : 0;
     d.bsw = (by && bw) ? perw : 0;
@@ -828,19 +838,32 @@ static bool to_micro(const CDesc &d, const char *arena, int esz, const unsigned 
 // Inner offset tables of the streaming kernels (computed once per node).
 static void absorb_table(const ADesc &d, std::vector<int32_t> &out) {
     const int nin = (int)d.nin, nod = d.nrd - d.nin_d;
-    out.assign((size_t)3 * nin, 0);
+    out.assign((size_t)4 * nin + d.nsh, 0);
     for (int i = 0; i < nin; ++i) {
-        int64_t r = i, x0 = 0, y0 = 0, w0 = 0;
+        int64_t r = i, x0 = 0, y0 = 0, w0 = 0, c0 = 0;
         for (int k = d.nrd - 1; k >= nod; --k) {
             int64_t dg = r % d.rsz[k];
             r /= d.rsz[k];
             x0 += dg * d.rsx[k];
             y0 += dg * d.rsy[k];
             w0 += dg * d.rsw[k];
+            c0 += dg * d.rshc[k];
         }
         out[i] = (int32_t)x0;
         out[nin + i] = (int32_t)y0;
         out[2 * nin + i] = (int32_t)w0;
+        out[3 * nin + i] = (int32_t)c0;
+    }
+    // W offset of each shared-label combination
+    for (int c = 0; c < d.nsh; ++c) {
+        int64_t r = c, w0 = 0;
+        for (int k = d.nrd - 1; k >= 0; --k) {
+            if (!d.rshc[k]) continue;
+            int64_t dg = r % d.rsz[k];
+            r /= d.rsz[k];
+            w0 += dg * d.rsw[k];
+        }
+        out[4 * nin + c] = (int32_t)w0;
     }
 }
 
@@ -857,6 +880,36 @@ static void reduce_table(const RDesc &d, std::vector<int32_t> &out) {
         }
         out[i] = (int32_t)x0;
         out[nin + i] = (int32_t)z0;
+    }
+}
+
+// TN_PLAN_TRACE=1 prints every step of a built program to stderr (one line
+// per step: direction, kernel family, shape parameters, algorithmic cost).
+static void trace_program(const Program &P) {
+    const char *e = getenv("TN_PLAN_TRACE");
+    if (!e || e[0] != '1') return;
+    int i = 0;
+    for (auto *steps : {&P.fsteps, &P.bsteps}) {
+        const char *dir = steps == &P.fsteps ? "fwd" : "bwd";
+        for (auto &st : *steps) {
+            if (st.kind == 2)
+                fprintf(stderr, "%s %d absorb ns %d nt %d nr %lld nin %lld nouter %lld beta %d",
+                        dir, i, st.ad.ns, st.ad.nt, (long long)st.ad.nr, (long long)st.ad.nin,
+                        (long long)st.ad.nouter, st.ad.nbeta);
+            else if (st.kind == 3)
+                fprintf(stderr, "%s %d reduce ns %d nt %d ng %lld nm %lld nin %lld beta %d", dir,
+                        i, st.rd.ns, st.rd.nt, (long long)st.rd.ng, (long long)st.rd.nm,
+                        (long long)st.rd.nin, st.rd.nbeta);
+            else if (st.kind == 1)
+                fprintf(stderr, "%s %d gemm%s b %lld m %lld n %lld k %lld", dir, i,
+                        st.g.tc ? "-tc" : "-simt", (long long)st.g.g.batch, (long long)st.g.g.R,
+                        (long long)st.g.g.C, (long long)st.g.g.K);
+            else
+                fprintf(stderr, "%s %d contract outs %lld k %lld", dir, i, (long long)st.d.nout_total,
+                        (long long)st.d.ktotal);
+            fprintf(stderr, " MB %.3f MFLOP %.3f\n", st.bytes / 1e6, st.flops / 1e6);
+            ++i;
+        }
     }
 }
 
@@ -1294,6 +1347,7 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
         CK(P.mem.alloc(&P.d_mb_beg, 4 * P.mb_beg.size()));
         CK(cudaMemcpy(P.d_mb_beg, P.mb_beg.data(), 4 * P.mb_beg.size(), cudaMemcpyHostToDevice));
     }
+    trace_program(P);
     // inner offset tables of the streaming steps, one device buffer
     {
         std::vector<int32_t> all, t;
@@ -1967,6 +2021,22 @@ tn_status tn_optimize_order(const tn_model *m, int method, int restarts, uint64_
     Tree t = optimize_tree(model_net(m->md, false), method, restarts, seed);
     std::copy(t.left.begin(), t.left.end(), left);
     std::copy(t.right.begin(), t.right.end(), right);
+    return TN_OK;
+}
+
+tn_status tn_reassociate(const tn_model *m, const int *left, const int *right, int *left_out,
+                         int *right_out) {
+    if (!m || !left || !right || !left_out || !right_out) return fail(TN_E_ARG, "NULL argument");
+    Net net = model_net(m->md, false);
+    Tree t;
+    t.nleaves = (int)net.leaf.size();
+    t.left.assign(left, left + t.nleaves - 1);
+    t.right.assign(right, right + t.nleaves - 1);
+    std::string err = validate_tree(t);
+    if (!err.empty()) return fail(TN_E_ORDER, err);
+    Tree r = reassociate_chains(net, t);
+    std::copy(r.left.begin(), r.left.end(), left_out);
+    std::copy(r.right.begin(), r.right.end(), right_out);
     return TN_OK;
 }
 

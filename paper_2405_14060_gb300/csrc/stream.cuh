@@ -31,7 +31,11 @@ struct ADesc {
     int mxx_bs, mxw_bs;
     unsigned long long *mxy;
     int32_t *argmax;                  // max-plus: flat summed index per output
-    const int32_t *tab;               // inner offsets: X [nin], Y [nin], W [nin] (device)
+    const int32_t *tab;               // inner offsets: X [nin], Y [nin], W [nin], then the
+                                      // shared-label index [nin] and the W offset of every
+                                      // shared-label combination [nsh] (device)
+    int nsh;                          // combinations of the labels W shares with X and Y
+    int32_t rshc[MAXD];               // per R dim: stride in that combination index (0: not in W)
 };
 
 // Reduce: O[g, s, t] = sum_m X[g, m, s] Z[g, m, t]

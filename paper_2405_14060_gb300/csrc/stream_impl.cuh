@@ -109,8 +109,140 @@ __global__ void __launch_bounds__(256) k_absorb(const __grid_constant__ ADesc d)
     if (SEMI == SUM && d.mxy) block_max_atomic(d.mxy + beta, (double)mx * (double)scale);
 }
 
+// Sum-product absorb with many (summed x new) combinations per position.
+// The small operand W is staged once per block in shared memory as dense
+// [shared combination][s][t] blocks (t fastest, zero-padded to NS x NT, one
+// padding quad between blocks to spread banks), so the inner loop is
+// register-blocked: each thread keeps its position's NS values of X in
+// registers and reads W a vector of t values at a time (VW FMAs per shared
+// load) instead of one global load per multiply-add.
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+    using V = float4;
+    static constexpr int W = 4;
+};
+template <>
+struct Vec<double> {
+    using V = double2;
+    static constexpr int W = 2;
+};
+
+template <typename T, int NS, int NT>
+__host__ __device__ constexpr int absorb_blk() {
+    return NS * NT + 16 / (int)sizeof(T);
+}
+
+template <typename T, int NS, int NT>
+__global__ void __launch_bounds__(256) k_absorb_sm(const __grid_constant__ ADesc d) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *smW = (T *)smraw;
+    constexpr int BLK = absorb_blk<T, NS, NT>();
+    constexpr int VW = NT < Vec<T>::W ? NT : Vec<T>::W;
+    constexpr int U = NS * NT <= 64 ? 2 : 1;
+    const int nin = (int)d.nin;
+    const int *tx = d.tab, *ty = d.tab + nin, *tc = d.tab + 3 * nin, *wsh = d.tab + 4 * nin;
+    const int nod = d.nrd - d.nin_d;
+    const int64_t beta = blockIdx.y;
+    {
+        const T *Wg = (const T *)d.W + beta * d.bsw;
+        const int tot = d.nsh * NS * NT;
+        for (int i = threadIdx.x; i < tot; i += 256) {
+            int c = i / (NS * NT), st = i - c * (NS * NT);
+            int si = st / NT, ti = st - si * NT;
+            T v = T(0);
+            if (si < d.ns && ti < d.nt) v = __ldg(Wg + wsh[c] + d.wso[si] + d.wto[ti]);
+            smW[c * BLK + st] = v;
+        }
+    }
+    __syncthreads();
+    T sx = d.mxx ? pow2neg<T>(exp_of_bits(d.mxx[beta * d.mxx_bs])) : T(1);
+    T sw = d.mxw ? pow2neg<T>(exp_of_bits(d.mxw[beta * d.mxw_bs])) : T(1);
+    const T scale = sx * sw;
+    T mx = 0;
+    for (int64_t o = blockIdx.x; o < d.nouter; o += gridDim.x) {
+        int64_t bx = beta * d.bsx, by = beta * d.bsy;
+        int cb = 0;
+        {
+            int64_t r = o;
+            for (int k = nod - 1; k >= 0; --k) {
+                int64_t dg = r % d.rsz[k];
+                r /= d.rsz[k];
+                bx += dg * d.rsx[k];
+                by += dg * d.rsy[k];
+                cb += (int)dg * d.rshc[k];
+            }
+        }
+        const T *Xb = (const T *)d.X + bx;
+        T *Yb = (T *)d.Y + by;
+        for (int j0 = threadIdx.x; j0 < nin; j0 += 256 * U) {
+            T x[U][NS];
+            int oy[U], oc[U];
+            bool on[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                int j = j0 + u * 256;
+                on[u] = j < nin;
+                int jj = on[u] ? j : 0;
+                int ox = __ldg(tx + jj);
+                oy[u] = __ldg(ty + jj);
+                oc[u] = (cb + __ldg(tc + jj)) * BLK;
+#pragma unroll
+                for (int s = 0; s < NS; ++s)
+                    x[u][s] = (on[u] && s < d.ns) ? Xb[ox + d.xoff[s]] : T(0);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (!on[u]) continue;
+                const T *w = smW + oc[u];
+                T *Y = Yb + oy[u];
+#pragma unroll
+                for (int t0 = 0; t0 < NT; t0 += VW) {
+                    if (t0 >= d.nt) break;
+                    T acc[VW];
+#pragma unroll
+                    for (int v = 0; v < VW; ++v) acc[v] = 0;
+#pragma unroll
+                    for (int s = 0; s < NS; ++s) {
+                        if (VW == Vec<T>::W) {
+                            typename Vec<T>::V wv = *(const typename Vec<T>::V *)(w + s * NT + t0);
+                            const T *wp = (const T *)&wv;
+#pragma unroll
+                            for (int v = 0; v < VW; ++v) acc[v] += x[u][s] * wp[v];
+                        } else {
+#pragma unroll
+                            for (int v = 0; v < VW; ++v) acc[v] += x[u][s] * w[s * NT + t0 + v];
+                        }
+                    }
+#pragma unroll
+                    for (int v = 0; v < VW; ++v) {
+                        if (t0 + v < d.nt) {
+                            Y[d.yoff[t0 + v]] = acc[v] * scale;
+                            mx = mx > acc[v] ? mx : acc[v];
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (d.mxy) block_max_atomic(d.mxy + beta, (double)mx * (double)scale);
+}
+
 template <typename T, int NS, int NT>
 static void absorb_go(const ADesc &d, int semiring, cudaStream_t st) {
+    constexpr int BLK = absorb_blk<T, NS, NT>();
+    const size_t smem = (size_t)d.nsh * BLK * sizeof(T);
+    if constexpr (NS * NT >= 16) {
+        if (semiring == SUM && smem <= 32768) {
+            // a few resident blocks per SM, each stages W once
+            int64_t cap = std::max<int64_t>(1, (152LL * 4) / std::max(1, d.nbeta));
+            dim3 grid((unsigned)std::max<int64_t>(1, std::min(d.nouter, cap)), (unsigned)d.nbeta,
+                      1);
+            k_absorb_sm<T, NS, NT><<<grid, 256, smem, st>>>(d);
+            return;
+        }
+    }
     int64_t cap = std::max<int64_t>(1, (152LL * 16) / std::max(1, d.nbeta));
     dim3 grid((unsigned)std::max<int64_t>(1, std::min(d.nouter, cap)), (unsigned)d.nbeta, 1);
     if (semiring == SUM) k_absorb<T, NS, NT, SUM><<<grid, 256, 0, st>>>(d);

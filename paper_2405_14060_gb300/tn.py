@@ -23,7 +23,8 @@ EXPORTS = ["tn_load_model", "tn_load_model_arrays", "tn_free_model", "tn_set_ord
            "tn_tree_from_elimination", "tn_optimize_order", "tn_tree_stats", "tn_pr",
            "tn_mar", "tn_map", "tn_mmap", "tn_sample", "tn_pr_dev", "tn_mar_dev",
            "tn_last_device_ms", "tn_last_launch_count", "tn_last_error", "tn_contract_dev",
-           "tn_profile", "tn_profile_steps", "tn_contract_dev_noalloc"]
+           "tn_profile", "tn_profile_steps", "tn_contract_dev_noalloc",
+           "tn_reassociate"]
 PROFILE_CLASSES = ["small", "absorb", "reduce", "tcgemm", "simtgemm", "prep", "generic", "unused7"]
 
 
@@ -187,6 +188,18 @@ class Model:
         r = np.zeros(self.nleaves - 1, np.int32)
         _ck(lib().tn_optimize_order(self._h, method, restarts, seed, _ptr(l), _ptr(r)))
         return l, r
+
+    def reassociate(self, left, right):
+        """Equivalent tree with runs of absorption steps re-associated (one
+        pass over the large tensor per run instead of one per step)."""
+        l = np.ascontiguousarray(left, np.int32)
+        r = np.ascontiguousarray(right, np.int32)
+        if l.shape != (self.nleaves - 1,) or r.shape != l.shape:
+            raise TNError(1, "tree needs nleaves-1 entries per array")
+        lo = np.zeros_like(l)
+        ro = np.zeros_like(r)
+        _ck(lib().tn_reassociate(self._h, _ptr(l), _ptr(r), _ptr(lo), _ptr(ro)))
+        return lo, ro
 
     def tree_stats(self, batch=1, prec="fp64"):
         out = np.zeros(6)

@@ -318,6 +318,34 @@ def test_workload2_full_size():
         m.tables[k] = t0
         fd = (lzs[0] - lzs[1]) / (2 * eps)
         assert abs(fd - (2 * sp[i][1] - 1)) < 1e-6
+    # the benchmark's tree: greedy with re-associated absorption chains
+    M.set_order(*M.reassociate(*M.optimize_order(0)))
+    lzr, margr = M.mar(prec="fp64")
+    assert abs(lzr[0] - lz_ref) < 1e-10 * max(1.0, abs(lz_ref)) * 10
+    assert np.max(np.abs(margr - marg64)) < 1e-10
+    for prec in ("tf32", "bf16", "fp32"):
+        lz, marg = M.mar(prec=prec)
+        assert abs(lz[0] - lz_ref) <= 1e-4 * abs(lz_ref), prec
+        assert np.max(np.abs(marg - marg64)) < 1e-3, prec
+        assert abs(M.pr(prec=prec)[0] - lz_ref) <= 1e-4 * abs(lz_ref), prec
+
+
+def test_reassociated_tree_batched_evidence():
+    """A re-associated tree (absorption runs contracted small-first) on a
+    14 x 14 grid with a batch of evidence sets: the combined small tensors
+    carry the batch label whenever an evidence vector joins them."""
+    m = synth.grid_ising(14, 3)
+    M = tn.Model.from_synth(m)
+    l, r = M.reassociate(*M.optimize_order(0))
+    M.set_order(l, r)
+    ev = synth.evidence_batch(m, 6, 0.1, 17)
+    for prec in ("fp64", "fp32"):
+        lz, marg = M.mar(ev, prec=prec)
+        for b in range(ev.shape[0]):
+            lzr, mr = oracle.ve_mar(m, ev[b])
+            tol = 1e-10 * max(1.0, abs(lzr)) if prec == "fp64" else 1e-4 * abs(lzr)
+            assert abs(lz[b] - lzr) <= tol, (prec, b)
+            _marg_close(M, marg[b], mr, 1e-10 if prec == "fp64" else 1e-3)
 
 
 def test_slicing_pr_mar_matches_oracle():

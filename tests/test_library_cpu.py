@@ -158,3 +158,66 @@ def test_slicing_reduces_space_complexity():
         M.set_order(l, r, slice_vars=[3, 3])
     with pytest.raises(tn.TNError):
         M.set_order(l, r, slice_vars=[m.nvars])
+
+
+def _tree_logz(m, left, right):
+    """log Z by contracting the model's tensors (plus unity vectors) along a
+    given tree with numpy.einsum in float64, max-normalising every
+    intermediate and keeping the log of the factor on the side."""
+    from collections import Counter
+    leaves = [list(map(int, s)) for s in m.scopes] + [[v] for v in range(m.nvars)]
+    total = Counter()
+    for L in leaves:
+        total.update(L)
+    ts = [np.asarray(t, float).reshape([int(m.card[v]) for v in s])
+          for s, t in zip(m.scopes, m.tables)]
+    ts += [np.ones(int(m.card[v])) for v in range(m.nvars)]
+    labels = [list(L) for L in leaves]
+    cnt = [Counter(L) for L in leaves]
+    logs = 0.0
+    for a, b in zip(left, right):
+        c = cnt[a] + cnt[b]
+        keep = [v for v in dict.fromkeys(labels[a] + labels[b]) if c[v] < total[v]]
+        idx = {v: i for i, v in enumerate(dict.fromkeys(labels[a] + labels[b]))}
+        out = np.einsum(ts[a], [idx[v] for v in labels[a]], ts[b], [idx[v] for v in labels[b]],
+                        [idx[v] for v in keep])
+        mx = float(np.max(out))
+        logs += np.log(mx)
+        ts.append(out / mx)
+        labels.append(keep)
+        cnt.append(Counter({v: c[v] for v in keep}))
+    return logs + float(np.log(np.sum(ts[-1])))
+
+
+def test_reassociate_keeps_the_contraction_and_cuts_read_write():
+    """Re-associated chains (associativity of the contraction, Sec. Tensor
+    networks): same log Z along both trees, fewer entries read and written,
+    same number of pairwise contractions."""
+    import oracle
+    m = synth.grid_ising(14, 3)
+    M = tn.Model.from_synth(m)
+    l, r = M.optimize_order(0)
+    M.set_order(l, r)
+    s0 = M.tree_stats(1, "fp32")
+    l2, r2 = M.reassociate(l, r)
+    assert (l2 != l).any() or (r2 != r).any()
+    M.set_order(l2, r2)                      # a valid tree
+    s1 = M.tree_stats(1, "fp32")
+    assert s1["nodes"] == s0["nodes"]
+    assert s1["rw"] < s0["rw"] - 0.5
+    assert s1["sc"] <= s0["sc"]
+    z0, z1 = _tree_logz(m, l, r), _tree_logz(m, l2, r2)
+    assert abs(z0 - z1) < 1e-10 * abs(z0)
+    assert abs(z1 - oracle.ve_pr(m)) < 1e-10 * abs(z1)
+    # nothing to do on small tensors: the tree comes back unchanged
+    ms = synth.grid_ising(6, 1)
+    Ms = tn.Model.from_synth(ms)
+    ls, rs = Ms.optimize_order(0)
+    l3, r3 = Ms.reassociate(ls, rs)
+    np.testing.assert_array_equal(l3, ls)
+    np.testing.assert_array_equal(r3, rs)
+    with pytest.raises(tn.TNError) as e:
+        bad = ls.copy()
+        bad[-1] = bad[0]
+        Ms.reassociate(bad, rs)
+    assert e.value.status == 3
