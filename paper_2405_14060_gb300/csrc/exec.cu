@@ -117,6 +117,7 @@ enum Cls { C_SMALL = 0, C_STREAM = 1, C_SPLITK = 2, C_TCGEMM = 3, C_SIMTGEMM = 4
 
 struct GemmOp {
     PDesc px, py, post;
+    std::vector<int32_t> tpx, tpy, tpost;   // tiled-permutation tables (host copies)
     bool has_post = false;
     bool direct = false;
     bool tc = false;
@@ -524,6 +525,9 @@ static std::string make_gemm_op(const std::vector<int> &card, int nbeta, int sto
         op.post_bytes = (double)B * R * C * ssz * 2;
         nd = (size_t)(B * R * C) * ssz;
     }
+    plan_permute_tiles(op.px, op.tpx);
+    plan_permute_tiles(op.py, op.tpy);
+    if (op.has_post) plan_permute_tiles(op.post, op.tpost);
     nx = (size_t)(B * R * Kld) * gsz;
     ny = (size_t)(B * C * Kld) * gsz;
     return "";
@@ -900,10 +904,20 @@ static void trace_program(const Program &P) {
                 fprintf(stderr, "%s %d reduce ns %d nt %d ng %lld nm %lld nin %lld beta %d", dir,
                         i, st.rd.ns, st.rd.nt, (long long)st.rd.ng, (long long)st.rd.nm,
                         (long long)st.rd.nin, st.rd.nbeta);
-            else if (st.kind == 1)
+            else if (st.kind == 1) {
                 fprintf(stderr, "%s %d gemm%s b %lld m %lld n %lld k %lld", dir, i,
                         st.g.tc ? "-tc" : "-simt", (long long)st.g.g.batch, (long long)st.g.g.R,
                         (long long)st.g.g.C, (long long)st.g.g.K);
+                auto pd = [](const char *nm, const PDesc &q) {
+                    fprintf(stderr, " | %s%s", nm, q.tl.tn > 0 ? "(tiled)" : "");
+                    for (int k = 0; k < q.nd; ++k)
+                        fprintf(stderr, " %d:%lld>%lld", q.sz[k], (long long)q.sin[k],
+                                (long long)q.sout[k]);
+                };
+                pd("px", st.g.px);
+                pd("py", st.g.py);
+                if (st.g.has_post) pd("post", st.g.post);
+            }
             else
                 fprintf(stderr, "%s %d contract outs %lld k %lld", dir, i, (long long)st.d.nout_total,
                         (long long)st.d.ktotal);
@@ -1352,8 +1366,19 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
     {
         std::vector<int32_t> all, t;
         std::vector<std::pair<Step *, size_t>> where;
+        std::vector<std::pair<PDesc *, size_t>> pwhere;
         for (auto *steps : {&P.fsteps, &P.bsteps})
             for (auto &st : *steps) {
+                if (st.kind == 1) {
+                    GemmOp &g = st.g;
+                    for (auto pr : {std::make_pair(&g.px, &g.tpx), std::make_pair(&g.py, &g.tpy),
+                                    std::make_pair(&g.post, &g.tpost)}) {
+                        if (pr.first->tl.tn <= 0) continue;
+                        pwhere.push_back({pr.first, all.size()});
+                        all.insert(all.end(), pr.second->begin(), pr.second->end());
+                    }
+                    continue;
+                }
                 if (st.kind == 2) absorb_table(st.ad, t);
                 else if (st.kind == 3) reduce_table(st.rd, t);
                 else continue;
@@ -1368,6 +1393,7 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                 if (w.first->kind == 2) w.first->ad.tab = dt + w.second;
                 else w.first->rd.tab = dt + w.second;
             }
+            for (auto &w : pwhere) w.first->tl.ttab = dt + w.second;
         }
     }
     // GEMM workspaces, then patch the steps' workspace pointers
@@ -2494,6 +2520,21 @@ tn_status tn_contract_dev(int nlabels, const int *sizes, int na, const int *labe
             CK(cudaMallocAsync(&wx, nx, st));
             CK(cudaMallocAsync(&wy, ny, st));
             if (nd) CK(cudaMallocAsync(&wd, nd, st));
+            // tiled-permutation tables: one device copy for the call
+            std::vector<int32_t> tall;
+            for (auto pr : {std::make_pair(&op.px, &op.tpx), std::make_pair(&op.py, &op.tpy),
+                            std::make_pair(&op.post, &op.tpost)}) {
+                if (pr.first->tl.tn <= 0) continue;
+                pr.first->tl.ttab = (const int32_t *)(uintptr_t)tall.size();   // offset for now
+                tall.insert(tall.end(), pr.second->begin(), pr.second->end());
+            }
+            int32_t *dtab = nullptr;
+            if (!tall.empty()) {
+                CK(cudaMallocAsync(&dtab, tall.size() * 4, st));
+                CK(cudaMemcpyAsync(dtab, tall.data(), tall.size() * 4, cudaMemcpyHostToDevice, st));
+                for (PDesc *q : {&op.px, &op.py, &op.post})
+                    if (q->tl.tn > 0) q->tl.ttab = dtab + (uintptr_t)q->tl.ttab;
+            }
             op.px.out = wx;
             op.py.out = wy;
             op.g.X = wx;
@@ -2518,6 +2559,11 @@ tn_status tn_contract_dev(int nlabels, const int *sizes, int na, const int *labe
             cudaFreeAsync(wx, st);
             cudaFreeAsync(wy, st);
             if (wd) cudaFreeAsync(wd, st);
+            if (dtab) {
+                // the pageable source of the table copy must outlive it
+                cudaStreamSynchronize(st);
+                cudaFreeAsync(dtab, st);
+            }
             if (le != cudaSuccess || e2 != cudaSuccess)
                 return fail(TN_E_CUDA, std::string("GEMM launch: ") +
                                            cudaGetErrorString(le != cudaSuccess ? le : e2));

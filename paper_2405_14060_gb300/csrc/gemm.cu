@@ -21,9 +21,11 @@
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <mutex>
+#include <vector>
 
 #include "devutil.cuh"
 #include "gemm.cuh"
@@ -32,26 +34,24 @@ namespace tn {
 
 // ------------------------------------------------------------- permute
 
-template <typename T> __device__ __forceinline__ double ld_as_double(const void *p, int64_t i);
-template <> __device__ __forceinline__ double ld_as_double<float>(const void *p, int64_t i) {
-    return (double)((const float *)p)[i];
-}
-template <> __device__ __forceinline__ double ld_as_double<double>(const void *p, int64_t i) {
-    return ((const double *)p)[i];
-}
+template <typename TI, int OT>
+__device__ __forceinline__ void store_conv(void *out, int64_t i, TI x);
 
+// Element-wise form: one element per thread and step, in the input type (the
+// scale is an exact power of two).
 template <typename TI, int OT>
 __global__ void __launch_bounds__(256) k_permute(const __grid_constant__ PDesc p, int64_t per) {
     // blockIdx.y = batch item when the outermost dimension is the batch label
     // and maxima are recorded (per = entries per item); else blockIdx.y = 0
     // and per = total.
     const int64_t item = blockIdx.y;
-    double mxv = 0;
-    constexpr int U = 4;
+    TI mxv = 0;
+    constexpr int U = 8;
+    const TI *in = (const TI *)p.in;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < per; i0 += stride * U) {
         int64_t oi[U], oo[U], beta[U];
-        double v[U];
+        TI v[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             int64_t i = i0 + u * stride;
@@ -78,23 +78,215 @@ __global__ void __launch_bounds__(256) k_permute(const __grid_constant__ PDesc p
             }
         }
 #pragma unroll
-        for (int u = 0; u < U; ++u) v[u] = ld_as_double<TI>(p.in, oi[u]);
+        for (int u = 0; u < U; ++u) v[u] = in[oi[u]];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (i0 + u * stride >= per) continue;
-            double x = v[u];
-            if (p.mxi) x *= pow2neg<double>(exp_of_bits(p.mxi[beta[u] * p.mxi_bs]));
-            if (OT == E_F64) ((double *)p.out)[oo[u]] = x;
-            else if (OT == E_F32) ((float *)p.out)[oo[u]] = (float)x;
-            else ((__nv_bfloat16 *)p.out)[oo[u]] = __float2bfloat16_rn((float)x);
-            mxv = fmax(mxv, x);
+            TI x = v[u];
+            if (p.mxi) x *= pow2neg<TI>(exp_of_bits(p.mxi[beta[u] * p.mxi_bs]));
+            store_conv<TI, OT>(p.out, oo[u], x);
+            mxv = mxv > x ? mxv : x;
         }
     }
-    if (p.mxo) block_max_atomic(p.mxo + item, mxv);
+    if (p.mxo) block_max_atomic(p.mxo + item, (double)mxv);
+}
+
+template <typename TI, int OT>
+__device__ __forceinline__ void store_conv(void *out, int64_t i, TI x) {
+    if (OT == E_F64) ((double *)out)[i] = (double)x;
+    else if (OT == E_F32) ((float *)out)[i] = (float)x;
+    else ((__nv_bfloat16 *)out)[i] = __float2bfloat16_rn((float)x);
+}
+
+template <typename TI, int OT>
+__global__ void __launch_bounds__(256) k_permute_tiled(const __grid_constant__ PDesc p,
+                                                       int64_t per_item) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    TI *sm = (TI *)smraw;
+    const PTile &t = p.tl;
+    const int64_t item = blockIdx.y;
+    const int n = t.tn;
+    const int32_t *tin = t.ttab, *tout = t.ttab + n, *slot = t.ttab + 2 * n;
+    const TI *in = (const TI *)p.in;
+    TI mxv = 0;
+    for (int64_t q = blockIdx.x; q < per_item; q += gridDim.x) {
+        int64_t bi = 0, bo = 0, beta = 0;
+        {
+            // tile counts stay below 2^31 (checked on the host): 32-bit digits
+            uint32_t g = (uint32_t)(item * per_item + q);
+            for (int k = t.nrest - 1; k >= 0; --k) {
+                uint32_t dg;
+                if (t.rsh[k] >= 0) {
+                    dg = g & (uint32_t)(t.rsz[k] - 1);
+                    g >>= t.rsh[k];
+                } else {
+                    dg = g % (uint32_t)t.rsz[k];
+                    g /= (uint32_t)t.rsz[k];
+                }
+                bi += (int64_t)dg * t.rin[k];
+                bo += (int64_t)dg * t.rout[k];
+                if (k == t.rest_beta) beta = dg;
+            }
+        }
+        for (int e0 = threadIdx.x; e0 < n; e0 += 1024) {
+            TI v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                int e = e0 + u * 256;
+                v[u] = e < n ? in[bi + __ldg(tin + e)] : TI(0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                int e = e0 + u * 256;
+                if (e < n) sm[e + (e >> 5)] = v[u];
+            }
+        }
+        __syncthreads();
+        const TI sc = p.mxi ? pow2neg<TI>(exp_of_bits(p.mxi[beta * p.mxi_bs])) : TI(1);
+        for (int e = threadIdx.x; e < n; e += 256) {
+            TI x = sm[__ldg(slot + e)] * sc;
+            store_conv<TI, OT>(p.out, bo + __ldg(tout + e), x);
+            mxv = mxv > x ? mxv : x;
+        }
+        __syncthreads();
+    }
+    if (p.mxo) block_max_atomic(p.mxo + item, (double)mxv);
+}
+
+void plan_permute_tiles(PDesc &p, std::vector<int32_t> &tab) {
+    p.tl.tn = 0;
+    tab.clear();
+    if (p.nd < 2 || p.total < 8192 || p.total / 64 >= (1LL << 31)) return;
+    struct D { int64_t sz, sin, sout; bool beta; };
+    std::vector<D> d;
+    for (int i = 0; i < p.nd; ++i) d.push_back({p.sz[i], p.sin[i], p.sout[i], i == p.beta_dim});
+    constexpr int64_t RUN = 32;
+    std::vector<char> in_u(d.size(), 0);
+    int64_t n = 1;
+    bool full = false;
+    // dims below `lim` on one side (lim < 0: the next input-fastest dims
+    // until the tile holds 2048 entries)
+    auto add_below = [&](bool by_in, int64_t lim) {
+        while (!full && (lim > 0 || n < 2048)) {
+            int best = -1;
+            for (int i = 0; i < (int)d.size(); ++i) {
+                if (in_u[i] || d[i].beta || d[i].sz < 2) continue;
+                int64_t st = by_in ? d[i].sin : d[i].sout;
+                if (lim > 0 && st >= lim) continue;
+                if (best < 0 || st < (by_in ? d[best].sin : d[best].sout)) best = i;
+            }
+            if (best < 0) return;
+            if (n * d[best].sz <= PT_MAXN) {
+                in_u[best] = 1;
+                n *= d[best].sz;
+                continue;
+            }
+            int64_t lo = PT_MAXN / n;
+            while (lo >= 2 && d[best].sz % lo) --lo;
+            if (lo >= 2) {
+                D hi{d[best].sz / lo, d[best].sin * lo, d[best].sout * lo, false};
+                D lw{lo, d[best].sin, d[best].sout, false};
+                d[best] = hi;
+                d.insert(d.begin() + best + 1, lw);
+                in_u.insert(in_u.begin() + best + 1, 1);
+                n *= lo;
+            }
+            full = true;
+        }
+    };
+    add_below(true, RUN);
+    add_below(false, RUN);
+    add_below(true, -1);
+    if (n < 256) return;
+    std::vector<int> U;
+    for (int i = 0; i < (int)d.size(); ++i)
+        if (in_u[i]) U.push_back(i);
+    auto order_by = [&](bool by_in) {
+        std::vector<int> o = U;
+        std::sort(o.begin(), o.end(), [&](int a, int b) {
+            return by_in ? d[a].sin < d[b].sin : d[a].sout < d[b].sout;
+        });
+        return o;   // fastest digit first
+    };
+    std::vector<int> oi = order_by(true), oo = order_by(false);
+    // digit vector -> index in the input order
+    std::vector<int64_t> wi(d.size(), 0);
+    {
+        int64_t w = 1;
+        for (int i : oi) {
+            wi[i] = w;
+            w *= d[i].sz;
+        }
+    }
+    tab.assign((size_t)3 * n, 0);
+    for (int64_t e = 0; e < n; ++e) {
+        int64_t r = e, off = 0;
+        for (int i : oi) {
+            int64_t dg = r % d[i].sz;
+            r /= d[i].sz;
+            off += dg * d[i].sin;
+        }
+        if (off >= (1LL << 31)) {
+            tab.clear();
+            return;
+        }
+        tab[e] = (int32_t)off;
+    }
+    for (int64_t e = 0; e < n; ++e) {
+        int64_t r = e, off = 0, ein = 0;
+        for (int i : oo) {
+            int64_t dg = r % d[i].sz;
+            r /= d[i].sz;
+            off += dg * d[i].sout;
+            ein += dg * wi[i];
+        }
+        if (off >= (1LL << 31)) {
+            tab.clear();
+            return;
+        }
+        tab[n + e] = (int32_t)off;
+        tab[2 * n + e] = (int32_t)(ein + (ein >> 5));
+    }
+    PTile &t = p.tl;
+    t.nrest = 0;
+    t.rest_beta = -1;
+    t.ntiles = 1;
+    for (int i = 0; i < (int)d.size(); ++i) {
+        if (in_u[i]) continue;
+        if (t.nrest >= MAXD) {
+            tab.clear();
+            return;
+        }
+        if (d[i].beta) t.rest_beta = t.nrest;
+        t.rsz[t.nrest] = (int32_t)d[i].sz;
+        t.rsh[t.nrest] = (d[i].sz & (d[i].sz - 1)) ? -1 : __builtin_ctzll((unsigned long long)d[i].sz);
+        t.rin[t.nrest] = d[i].sin;
+        t.rout[t.nrest] = d[i].sout;
+        t.ntiles *= d[i].sz;
+        ++t.nrest;
+    }
+    // per-item maxima need the batch dim outermost (one item per grid row)
+    if ((p.mxo && t.rest_beta > 0) || t.ntiles >= (1LL << 31)) {
+        tab.clear();
+        return;
+    }
+    t.tn = (int)n;
+    t.ttab = nullptr;   // device copy of `tab`, set by the caller
 }
 
 void launch_permute(const PDesc &p, cudaStream_t st) {
     if (p.total <= 0) return;
+    if (p.tl.tn > 0 && p.tl.ttab) {
+        int nitems = (p.mxo && p.tl.rest_beta == 0) ? p.tl.rsz[0] : 1;
+        int64_t per = p.tl.ntiles / nitems;
+        int64_t cap = std::max<int64_t>(1, (152LL * 8) / nitems);
+        dim3 grid((unsigned)std::max<int64_t>(1, std::min(per, cap)), (unsigned)nitems, 1);
+        size_t sm = (size_t)(p.tl.tn + p.tl.tn / 32 + 1) * (p.in_type == E_F64 ? 8 : 4);
+        if (p.in_type == E_F64) k_permute_tiled<double, E_F64><<<grid, 256, sm, st>>>(p, per);
+        else if (p.out_type == E_F32) k_permute_tiled<float, E_F32><<<grid, 256, sm, st>>>(p, per);
+        else k_permute_tiled<float, E_BF16><<<grid, 256, sm, st>>>(p, per);
+        return;
+    }
     int nitems = 1;
     if (p.mxo && p.beta_dim == 0) nitems = p.sz[0];
     int64_t per = p.total / nitems;
@@ -272,7 +464,7 @@ __global__ void __launch_bounds__(128, 1)
     have = __all_sync(0xffffffffu, have);
     tc_fence_after();
     const int64_t row = m0 + warp * 32 + lane;
-    double mx = 0;
+    float mx = 0;
     if (have) {
         float *drow = p.D + (int64_t)bz * p.bsd + row * p.ldd;
         for (int ch = 0; ch < TC_BN / 32; ++ch) {
@@ -302,13 +494,13 @@ __global__ void __launch_bounds__(128, 1)
                         v.z = __uint_as_float(r[4 * q + 2]);
                         v.w = __uint_as_float(r[4 * q + 3]);
                         dst[q] = v;
-                        mx = fmax(mx, (double)fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
+                        mx = fmaxf(mx, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
                     }
                 } else {
                     for (int q = 0; q < 32 && c0 + q < p.C; ++q) {
                         float v = __uint_as_float(r[q]);
                         drow[c0 + q] = v;
-                        mx = fmax(mx, (double)v);
+                        mx = fmaxf(mx, v);
                     }
                 }
             }
@@ -317,7 +509,7 @@ __global__ void __launch_bounds__(128, 1)
     int64_t beta = p.beta_div_batch > 0 ? (int64_t)bz / p.beta_div_batch
                    : p.beta_div_row > 0 ? (row < p.R ? row : p.R - 1) / p.beta_div_row
                                         : 0;
-    record_max(p.mxd, beta, have && row < p.R, mx);
+    record_max(p.mxd, beta, have && row < p.R, (double)mx);
     tc_fence_before();
     __syncthreads();
     if (warp == 2)
@@ -434,7 +626,7 @@ __global__ void __launch_bounds__(256) k_simt_gemm(const __grid_constant__ GDesc
         }
         __syncthreads();
     }
-    double mx = 0;
+    T mx = 0;
     T *D = (T *)g.D + b * g.bsd;
     int64_t rowlast = r0 + ty * 4;
 #pragma unroll
@@ -447,7 +639,7 @@ __global__ void __launch_bounds__(256) k_simt_gemm(const __grid_constant__ GDesc
             int64_t c = c0 + tx * 4 + j;
             if (c < g.C) {
                 D[r * g.ldd + c] = acc[i][j];
-                mx = fmax(mx, (double)acc[i][j]);
+                mx = mx > acc[i][j] ? mx : acc[i][j];
             }
         }
     }
@@ -469,7 +661,7 @@ __global__ void __launch_bounds__(256) k_simt_gemm(const __grid_constant__ GDesc
         }
         return;
     }
-    record_max(g.mxd, beta, any, mx);
+    record_max(g.mxd, beta, any, (double)mx);
 }
 
 void launch_simt_gemm(const GDesc &g, cudaStream_t st) {

@@ -6,6 +6,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "kernels.cuh"
 
 namespace tn {
@@ -17,6 +19,23 @@ enum ElemType { E_F64 = 0, E_F32 = 1, E_BF16 = 2 };
 //   logical dims (slowest first): sz[d]; input stride sin[d]; output stride sout[d]
 //   beta_dim: the dimension that indexes batch items for the scale (-1: none)
 //   mxo (optional): record the per-item maximum of the output (beta from beta_dim)
+// Tiled form of a permutation (chosen on the host when it pays): every dim
+// whose input or output stride is below 32 elements goes into one tile of
+// tn <= 4096 entries staged in shared memory, so that loads run along the
+// input's contiguous runs and stores along the output's; the other dims
+// enumerate the tiles.  Device table ttab: input offsets [tn] (input order),
+// output offsets [tn] (output order), and for each output-order entry its
+// padded shared-memory slot [tn].
+constexpr int PT_MAXN = 4096;
+struct PTile {
+    int tn;                          // 0: not tiled
+    int nrest, rest_beta;            // rest dims, index of the batch dim among them (-1)
+    int32_t rsz[MAXD], rsh[MAXD];    // rest sizes, log2 (-1: not a power of two)
+    int64_t rin[MAXD], rout[MAXD];
+    int64_t ntiles;
+    const int32_t *ttab;
+};
+
 struct PDesc {
     int nd;
     int pow2;
@@ -30,7 +49,12 @@ struct PDesc {
     const unsigned long long *mxi;   // scale source (NULL: no scaling)
     int mxi_bs;                      // 1: per item
     unsigned long long *mxo;
+    PTile tl;
 };
+
+// Choose the tiled form for p when it pays (host): fills p.tl (but for the
+// device table pointer) and the table; leaves p.tl.tn = 0 otherwise.
+void plan_permute_tiles(PDesc &p, std::vector<int32_t> &tab);
 
 // D[b][r][c] = sum_k X[b][r][k] * Y[b][c][k]   (X, Y K-major, D row-major FP32/FP64)
 struct GDesc {

@@ -68,7 +68,7 @@ __device__ __forceinline__ void decode_k(const CDesc &d, int64_t k, int64_t &ka,
 template <typename T, int SEMI>
 __global__ void __launch_bounds__(256) k_contract(const __grid_constant__ CDesc d) {
     const int64_t beta = blockIdx.y;
-    double mx = 0;
+    T mx = 0;
     T sa = T(1), sb = T(1);
     if (SEMI == SUM) {
         sa = d.mxa ? pow2neg<T>(exp_of_bits(d.mxa[beta * d.mxa_bs])) : T(1);
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256) k_contract(const __grid_constant__ CDesc 
                 }
             }
             ((T *)d.C)[idx] = acc;
-            mx = fmax(mx, (double)acc);
+            mx = mx > acc ? mx : acc;
         } else {
             T best = -INFINITY;
             int32_t bk = 0;
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(256) k_contract(const __grid_constant__ CDesc 
             if (d.argmax) d.argmax[idx] = bk;
         }
     }
-    if (SEMI == SUM && d.mxc) block_max_atomic(d.mxc + beta, mx);
+    if (SEMI == SUM && d.mxc) block_max_atomic(d.mxc + beta, (double)mx);
 }
 
 // ---------------------------------------------------------------- split-K

@@ -232,6 +232,12 @@ GEMM_CASES = [
     ([4, 4, 4, 4, 4, 4, 2], [0, 1, 2, 3], [2, 3, 4, 5, 6], [4, 5, 6, 0, 1]),
     # several tiles in every direction: m = 512, n = 768, k = 384
     ([8, 64, 3, 256, 128, 3], [0, 1, 4, 5], [4, 5, 2, 3], [0, 1, 2, 3]),
+    # row operand stored K-slow (its preparation is a tiled transpose), output
+    # [n][m] (scatter through a tiled transpose)
+    ([2] * 20, list(range(6, 14)) + list(range(6)), list(range(14, 20)) + list(range(6, 14)),
+     list(range(14, 20)) + list(range(6))),
+    # interleaved non-binary labels on both operands and the output
+    ([3, 25, 7, 36, 9, 30], [2, 0, 3, 1], [3, 5, 2, 4], [5, 0, 4, 1]),
 ]
 GEMM_TOL = {"fp64": 1e-12, "fp32": 1e-5, "tf32": 2e-3, "bf16": 1.5e-2}
 
