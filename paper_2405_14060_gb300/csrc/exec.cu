@@ -150,6 +150,8 @@ struct Program {
     std::vector<int64_t> am_off;
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
+    unsigned int *rcnt = nullptr;   // reduce steps' per-group completion counters
+    int64_t nrcnt = 0;
     LeafRec *d_leaf = nullptr;
     int nleafrec = 0;
     int64_t *d_exps = nullptr;
@@ -1415,6 +1417,18 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
         }
     P.scratch_bytes = scratch;
     if (scratch) CK(P.mem.alloc(&P.scratch, scratch));
+    // completion counters of the reduce steps (one per group and item)
+    P.nrcnt = 0;
+    for (auto *steps : {&P.fsteps, &P.bsteps})
+        for (auto &st : *steps)
+            if (st.kind == 3) P.nrcnt = std::max<int64_t>(P.nrcnt, st.rd.ng * st.rd.nbeta);
+    if (P.nrcnt) {
+        CK(P.mem.alloc(&P.rcnt, (size_t)P.nrcnt * 4));
+        CK(cudaMemset(P.rcnt, 0, (size_t)P.nrcnt * 4));
+        for (auto *steps : {&P.fsteps, &P.bsteps})
+            for (auto &st : *steps)
+                if (st.kind == 3) st.rd.cnt = P.rcnt;
+    }
     // ---- leaf records to device
     CK(P.mem.alloc(&P.d_leaf, sizeof(LeafRec) * n));
     CK(cudaMemcpy(P.d_leaf, P.leafrec.data(), sizeof(LeafRec) * n, cudaMemcpyHostToDevice));
@@ -1619,6 +1633,7 @@ void enqueue_program(tn_model *m, Program &P, cudaStream_t st, Prof *pr = nullpt
     const bool maxplus = P.kind == K_MAP || P.kind == K_MAXNET;
     int nl = 0;
     cudaMemsetAsync(P.mx, 0, (size_t)P.nmx * 8, st);
+    if (P.nrcnt) cudaMemsetAsync(P.rcnt, 0, (size_t)P.nrcnt * 4, st);
     ++nl;
     launch_leaves<T>(P.d_leaf, P.nleafrec, m->d_tables, P.d_card, m->md.nvars, P.d_evid, P.nbeta,
                      maxplus ? 1 : 0, (T *)P.arena, P.mx, m->d_flags, P.d_slice_val, st);

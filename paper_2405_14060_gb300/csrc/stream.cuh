@@ -62,6 +62,7 @@ struct RDesc {
     int mxx_bs, mxz_bs;
     unsigned long long *mxo;
     const int32_t *tab;               // inner offsets: X [nin], Z [nin] (device)
+    unsigned int *cnt;                // per group: blocks done (zero between launches)
 };
 
 template <typename T>

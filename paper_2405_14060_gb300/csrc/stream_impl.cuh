@@ -11,8 +11,9 @@
 //                  of the maximiser (Eq. tropical).
 //   k_reduce_part  each block streams a chunk of the summed positions m of one
 //                  group g and accumulates the outer products X[g,m,s] Z[g,m,t]
-//                  in registers; k_reduce_fin sums the chunk partials in a
-//                  fixed order (deterministic) and records the maxima.
+//                  in registers; the group's last block to finish sums the
+//                  chunk partials in a fixed order (deterministic), writes the
+//                  result and records its maximum.
 #include <cmath>
 
 #pragma once
@@ -44,7 +45,12 @@ __global__ void __launch_bounds__(256) k_absorb(const __grid_constant__ ADesc d)
         T sw = d.mxw ? pow2neg<T>(exp_of_bits(d.mxw[beta * d.mxw_bs])) : T(1);
         scale = sx * sw;
     }
-    for (int64_t o = blockIdx.x; o < d.nouter; o += gridDim.x) {
+    // tiles: (outer index, chunk of 256 U inner positions)
+    const int nch = (nin + 256 * U - 1) / (256 * U);
+    const int64_t ntile = d.nouter * nch;
+    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const int64_t o = tile / nch;
+        const int c = (int)(tile - o * nch);
         int64_t bx = beta * d.bsx, by = beta * d.bsy, bw = beta * d.bsw;
         {
             int64_t r = o;
@@ -59,7 +65,8 @@ __global__ void __launch_bounds__(256) k_absorb(const __grid_constant__ ADesc d)
         const T *Xb = (const T *)d.X + bx;
         const T *Wb = (const T *)d.W + bw;
         T *Yb = (T *)d.Y + by;
-        for (int j0 = threadIdx.x; j0 < nin; j0 += 256 * U) {
+        {
+            const int j0 = c * 256 * U + threadIdx.x;
             T x[U][NS];
             int oy[U], ow[U];
             bool on[U];
@@ -161,7 +168,11 @@ __global__ void __launch_bounds__(256) k_absorb_sm(const __grid_constant__ ADesc
     T sw = d.mxw ? pow2neg<T>(exp_of_bits(d.mxw[beta * d.mxw_bs])) : T(1);
     const T scale = sx * sw;
     T mx = 0;
-    for (int64_t o = blockIdx.x; o < d.nouter; o += gridDim.x) {
+    const int nch = (nin + 256 * U - 1) / (256 * U);
+    const int64_t ntile = d.nouter * nch;
+    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const int64_t o = tile / nch;
+        const int c = (int)(tile - o * nch);
         int64_t bx = beta * d.bsx, by = beta * d.bsy;
         int cb = 0;
         {
@@ -176,7 +187,8 @@ __global__ void __launch_bounds__(256) k_absorb_sm(const __grid_constant__ ADesc
         }
         const T *Xb = (const T *)d.X + bx;
         T *Yb = (T *)d.Y + by;
-        for (int j0 = threadIdx.x; j0 < nin; j0 += 256 * U) {
+        {
+            const int j0 = c * 256 * U + threadIdx.x;
             T x[U][NS];
             int oy[U], oc[U];
             bool on[U];
@@ -236,15 +248,18 @@ static void absorb_go(const ADesc &d, int semiring, cudaStream_t st) {
     if constexpr (NS * NT >= 16) {
         if (semiring == SUM && smem <= 32768) {
             // a few resident blocks per SM, each stages W once
+            constexpr int U = NS * NT <= 64 ? 2 : 1;
+            int64_t ntile = d.nouter * ((d.nin + 256 * U - 1) / (256 * U));
             int64_t cap = std::max<int64_t>(1, (152LL * 4) / std::max(1, d.nbeta));
-            dim3 grid((unsigned)std::max<int64_t>(1, std::min(d.nouter, cap)), (unsigned)d.nbeta,
-                      1);
+            dim3 grid((unsigned)std::max<int64_t>(1, std::min(ntile, cap)), (unsigned)d.nbeta, 1);
             k_absorb_sm<T, NS, NT><<<grid, 256, smem, st>>>(d);
             return;
         }
     }
+    constexpr int U = NS * NT <= 4 ? 8 : NS * NT <= 16 ? 4 : NS * NT <= 64 ? 2 : 1;
+    int64_t ntile = d.nouter * ((d.nin + 256 * U - 1) / (256 * U));
     int64_t cap = std::max<int64_t>(1, (152LL * 16) / std::max(1, d.nbeta));
-    dim3 grid((unsigned)std::max<int64_t>(1, std::min(d.nouter, cap)), (unsigned)d.nbeta, 1);
+    dim3 grid((unsigned)std::max<int64_t>(1, std::min(ntile, cap)), (unsigned)d.nbeta, 1);
     if (semiring == SUM) k_absorb<T, NS, NT, SUM><<<grid, 256, 0, st>>>(d);
     else k_absorb<T, NS, NT, MAXPLUS><<<grid, 256, 0, st>>>(d);
 }
@@ -367,6 +382,7 @@ __global__ void __launch_bounds__(256) k_reduce_part(const __grid_constant__ RDe
         }
     }
     __shared__ T red[8][NS * NT];
+    __shared__ bool last;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int s = 0; s < NS; ++s)
@@ -383,39 +399,37 @@ __global__ void __launch_bounds__(256) k_reduce_part(const __grid_constant__ RDe
         for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += red[q][i];
         part[(g * nchunks + blockIdx.x) * (8 * 8) + i] = v * (sx * sz);
     }
-}
-
-template <typename T, int NS, int NT>
-__global__ void __launch_bounds__(256) k_reduce_fin(const __grid_constant__ RDesc d, int nchunks,
-                                                    const T *part) {
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t tot = d.ng * d.nbeta * NS * NT;
-    bool active = idx < tot;
-    int64_t beta = 0;
-    double v = 0;
-    if (active) {
-        int64_t g = idx / (NS * NT);
-        int i = (int)(idx - g * (NS * NT));
-        int s = i / NT, t = i % NT;
-        beta = g / d.ng;
-        if (s < d.ns && t < d.nt) {
-            T acc = 0;
-            for (int c = 0; c < nchunks; ++c) acc += part[(g * nchunks + c) * (8 * 8) + i];
-            int64_t ox = 0, oz = 0, oo = beta * d.bso;
-            group_offsets(d, g - beta * d.ng, ox, oz, oo);
-            ((T *)d.O)[oo + d.oso[s] + d.oto[t]] = acc;
-            v = (double)acc;
-        } else {
-            active = false;
+    // the group's last block to finish sums the chunk partials (fixed order:
+    // lane-strided chunks, then a shuffle tree), writes O and its maximum
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(d.cnt + g, 1u) == (unsigned)(nchunks - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    T mx = 0;
+    int64_t ox = 0, oz = 0, oo = beta * d.bso;
+    group_offsets(d, gi, ox, oz, oo);
+    for (int i = w; i < NS * NT; i += (int)(blockDim.x >> 5)) {
+        const int s = i / NT, t = i - (i / NT) * NT;
+        if (s >= d.ns || t >= d.nt) continue;
+        T v = 0;
+        for (int c = lane; c < nchunks; c += 32) v += __ldcg(part + (g * nchunks + c) * (8 * 8) + i);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) {
+            ((T *)d.O)[oo + d.oso[s] + d.oto[t]] = v;
+            mx = mx > v ? mx : v;
         }
     }
-    record_max(d.mxo, beta, active, v);
+    if (d.mxo) block_max_atomic(d.mxo + beta, (double)mx);
+    if (threadIdx.x == 0) d.cnt[g] = 0u;
 }
 
 static void reduce_shape(const RDesc &d, int64_t &chunk, int &nchunks) {
     int64_t groups = d.ng * d.nbeta;
     int64_t ntile = d.nouter * ((d.nin + 1023) / 1024);
-    int64_t want = std::max<int64_t>(1, (152LL * 8) / std::max<int64_t>(1, groups));
+    int64_t want = std::max<int64_t>(1, (152LL * 4) / std::max<int64_t>(1, groups));
     chunk = std::max<int64_t>(1, (ntile + want - 1) / want);
     nchunks = (int)((ntile + chunk - 1) / chunk);
 }
@@ -438,9 +452,6 @@ static void reduce_go(const RDesc &d, void *scratch, cudaStream_t st) {
     dim3 grid((unsigned)nchunks, (unsigned)std::min<int64_t>(groups, 65535),
               (unsigned)((groups + 65534) / 65535));
     k_reduce_part<T, NS, NT><<<grid, 256, 0, st>>>(d, chunk, nchunks, (T *)scratch);
-    int64_t tot = groups * NS * NT;
-    k_reduce_fin<T, NS, NT><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(d, nchunks,
-                                                                           (const T *)scratch);
 }
 
 template <typename T, int NS>
@@ -482,7 +493,7 @@ void launch_reduce(const RDesc &d, void *scratch, cudaStream_t st) {
 }
 
 #ifdef TN_STREAM_HOST_DEFS
-int reduce_launches(const RDesc &d) { return 2 * ((d.ns + 7) / 8) * ((d.nt + 7) / 8); }
+int reduce_launches(const RDesc &d) { return ((d.ns + 7) / 8) * ((d.nt + 7) / 8); }
 #endif
 
 
