@@ -21,6 +21,29 @@ template <> __device__ __forceinline__ double pow2neg<double>(int e) {
     return __longlong_as_double((long long)(1023 - e) << 52);
 }
 
+// Asynchronous global -> shared copies (one element per call) and their
+// commit / wait groups; a thread that only reads the shared slots it copied
+// itself needs no barrier, only the wait.
+__device__ __forceinline__ void cp_async_el(float *smem, const float *gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_el(double *smem, const double *gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 __device__ __forceinline__ unsigned long long dbits(double x) {
     return (unsigned long long)__double_as_longlong(x);
 }

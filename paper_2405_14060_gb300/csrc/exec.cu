@@ -898,14 +898,33 @@ static void trace_program(const Program &P) {
     for (auto *steps : {&P.fsteps, &P.bsteps}) {
         const char *dir = steps == &P.fsteps ? "fwd" : "bwd";
         for (auto &st : *steps) {
-            if (st.kind == 2)
-                fprintf(stderr, "%s %d absorb ns %d nt %d nr %lld nin %lld nouter %lld beta %d",
-                        dir, i, st.ad.ns, st.ad.nt, (long long)st.ad.nr, (long long)st.ad.nin,
-                        (long long)st.ad.nouter, st.ad.nbeta);
-            else if (st.kind == 3)
+            if (st.kind == 2) {
+                const ADesc &a = st.ad;
+                fprintf(stderr, "%s %d absorb ns %d nt %d nr %lld nin %lld nouter %lld beta %d nsh %d",
+                        dir, i, a.ns, a.nt, (long long)a.nr, (long long)a.nin,
+                        (long long)a.nouter, a.nbeta, a.nsh);
+                fprintf(stderr, " xoff");
+                for (int k = 0; k < a.ns && k < 8; ++k) fprintf(stderr, ",%d", a.xoff[k]);
+                fprintf(stderr, " yoff");
+                for (int k = 0; k < a.nt && k < 8; ++k) fprintf(stderr, ",%d", a.yoff[k]);
+                fprintf(stderr, " rdims");
+                for (int k = 0; k < a.nrd; ++k)
+                    fprintf(stderr, ",%d:%lld/%lld/%lld", a.rsz[k], (long long)a.rsx[k],
+                            (long long)a.rsy[k], (long long)a.rsw[k]);
+            } else if (st.kind == 3) {
+                const RDesc &r = st.rd;
                 fprintf(stderr, "%s %d reduce ns %d nt %d ng %lld nm %lld nin %lld beta %d", dir,
-                        i, st.rd.ns, st.rd.nt, (long long)st.rd.ng, (long long)st.rd.nm,
-                        (long long)st.rd.nin, st.rd.nbeta);
+                        i, r.ns, r.nt, (long long)r.ng, (long long)r.nm, (long long)r.nin,
+                        r.nbeta);
+                fprintf(stderr, " xoff");
+                for (int k = 0; k < r.ns && k < 8; ++k) fprintf(stderr, ",%lld", (long long)r.xoff[k]);
+                fprintf(stderr, " zoff");
+                for (int k = 0; k < r.nt && k < 8; ++k) fprintf(stderr, ",%lld", (long long)r.zoff[k]);
+                fprintf(stderr, " mdims");
+                for (int k = 0; k < r.nmd; ++k)
+                    fprintf(stderr, ",%d:%lld/%lld", r.msz[k], (long long)r.msx[k],
+                            (long long)r.msz2[k]);
+            }
             else if (st.kind == 1) {
                 fprintf(stderr, "%s %d gemm%s b %lld m %lld n %lld k %lld", dir, i,
                         st.g.tc ? "-tc" : "-simt", (long long)st.g.g.batch, (long long)st.g.g.R,

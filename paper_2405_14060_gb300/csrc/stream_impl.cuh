@@ -18,6 +18,8 @@
 
 #pragma once
 #include <algorithm>
+#include <mutex>
+#include <vector>
 
 #include "devutil.cuh"
 #include "stream.cuh"
@@ -52,7 +54,15 @@ __global__ void __launch_bounds__(256) k_absorb(const __grid_constant__ ADesc d)
         const int64_t o = tile / nch;
         const int c = (int)(tile - o * nch);
         int64_t bx = beta * d.bsx, by = beta * d.bsy, bw = beta * d.bsw;
-        {
+        if (d.pow2r) {
+            const int64_t r0 = o * nin;
+            for (int k = 0; k < nod; ++k) {
+                int64_t dg = (r0 >> d.rsh[k]) & (int64_t)(d.rsz[k] - 1);
+                bx += dg * d.rsx[k];
+                by += dg * d.rsy[k];
+                bw += dg * d.rsw[k];
+            }
+        } else {
             int64_t r = o;
             for (int k = nod - 1; k >= 0; --k) {
                 int64_t dg = r % d.rsz[k];
@@ -175,7 +185,15 @@ __global__ void __launch_bounds__(256) k_absorb_sm(const __grid_constant__ ADesc
         const int c = (int)(tile - o * nch);
         int64_t bx = beta * d.bsx, by = beta * d.bsy;
         int cb = 0;
-        {
+        if (d.pow2r) {
+            const int64_t r0 = o * nin;
+            for (int k = 0; k < nod; ++k) {
+                int64_t dg = (r0 >> d.rsh[k]) & (int64_t)(d.rsz[k] - 1);
+                bx += dg * d.rsx[k];
+                by += dg * d.rsy[k];
+                cb += (int)dg * d.rshc[k];
+            }
+        } else {
             int64_t r = o;
             for (int k = nod - 1; k >= 0; --k) {
                 int64_t dg = r % d.rsz[k];
@@ -317,11 +335,34 @@ __device__ __forceinline__ void group_offsets(const RDesc &d, int64_t gi, int64_
 }
 
 // The summed positions m split into inner ones (offset table computed at plan
-// time, at most A_INNER) and outer ones; blocks take contiguous ranges of
-// (outer index, inner chunk) tiles of one group.
+// time, at most A_INNER) and outer ones.  A block's 256 threads form nb =
+// nbs x nbt sub-blocks of pp = 256 / nb threads: thread (b, p) owns position p
+// of every staged tile and the NS x NT outputs (bs NS + s, bt NT + t) of its
+// sub-block b = (bs, bt), so outputs up to 32 x 32 need one pass over the
+// operands (threads of different sub-blocks fetch the same position's values
+// separately; the repeats hit L1).  Each thread's operand values for tiles of
+// pp positions (outer index, inner chunk) come into its own shared-memory
+// slots by asynchronous copies red_stages() tiles ahead of use (no barrier);
+// blocks take contiguous tile ranges of one group, write per-block partials,
+// and the group's last block to finish sums them in a fixed order
+// (deterministic), writes O and records its maximum.
+template <typename T>
+__host__ __device__ constexpr int red_stages() {
+    return sizeof(T) == 8 ? 3 : 4;
+}
+
+
 template <typename T, int NS, int NT>
-__global__ void __launch_bounds__(256) k_reduce_part(const __grid_constant__ RDesc d,
-                                                     int64_t chunk, int nchunks, T *part) {
+__global__ void __launch_bounds__(256) k_reduce_part(const __grid_constant__ RDesc d, int nbs,
+                                                     int nbt, int64_t chunk, int nchunks,
+                                                     int pstride, T *part) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    constexpr int S = red_stages<T>(), W = NS + NT;
+    // [S][W][256]: each thread stages (and later reads) only its own slots
+    T *buf = (T *)smraw + threadIdx.x;
+    const int nb = nbs * nbt, pp = 256 / nb;
+    const int sub = threadIdx.x / pp, p = threadIdx.x - sub * pp;
+    const int bs = sub / nbt, bt = sub - bs * nbt;
     const int nin = (int)d.nin;
     const int *tx = d.tab, *tz = d.tab + nin;
     const int nod = d.nmd - d.nin_d;
@@ -337,50 +378,75 @@ __global__ void __launch_bounds__(256) k_reduce_part(const __grid_constant__ RDe
     for (int s = 0; s < NS; ++s)
 #pragma unroll
         for (int t = 0; t < NT; ++t) acc[s][t] = 0;
-    // tiles: (outer index, inner chunk of 1024)
-    const int64_t cper = (nin + 1023) / 1024;
+    const int64_t cper = (nin + pp - 1) / pp;
     const int64_t ntile = d.nouter * cper;
-    const int64_t t0 = (int64_t)blockIdx.x * chunk, t1 = min(t0 + chunk, ntile);
-    constexpr int U = NS * NT <= 4 ? 8 : NS * NT <= 16 ? 4 : NS * NT <= 32 ? 2 : 1;
-    for (int64_t tile = t0; tile < t1; ++tile) {
-        int64_t o = tile / cper;
-        int c = (int)(tile - o * cper);
-        int64_t bx = gx, bz = gz;
-        {
-            int64_t r = o;
-            for (int k = nod - 1; k >= 0; --k) {
-                int64_t dg = r % d.msz[k];
-                r /= d.msz[k];
-                bx += dg * d.msx[k];
-                bz += dg * d.msz2[k];
+    const int64_t t0 = (int64_t)blockIdx.x * chunk;
+    const int64_t t1 = t0 + chunk < ntile ? t0 + chunk : ntile;
+    const int nk = t1 > t0 ? (int)(t1 - t0) : 0;
+    const T *X = (const T *)d.X, *Z = (const T *)d.Z;
+    const int s0 = bs * NS, z0 = bt * NT;
+    auto issue = [&](int k) {
+        T *sb = buf + (k % S) * W * 256;
+        const int64_t tile = t0 + k;
+        const int64_t o = tile / cper;
+        const int j = (int)(tile - o * cper) * pp + p;
+        if (j < nin) {
+            int64_t bx = gx, bz = gz;
+            if (d.pow2m) {
+                const int64_t r0 = o * nin;
+                for (int q = 0; q < nod; ++q) {
+                    int64_t dg = (r0 >> d.msh[q]) & (int64_t)(d.msz[q] - 1);
+                    bx += dg * d.msx[q];
+                    bz += dg * d.msz2[q];
+                }
+            } else {
+                int64_t r = o;
+                for (int q = nod - 1; q >= 0; --q) {
+                    int64_t dg = r % d.msz[q];
+                    r /= d.msz[q];
+                    bx += dg * d.msx[q];
+                    bz += dg * d.msz2[q];
+                }
             }
-        }
-        const T *X = (const T *)d.X + bx;
-        const T *Z = (const T *)d.Z + bz;
-        const int jend = min(nin, (c + 1) * 1024);
-        for (int j0 = c * 1024 + threadIdx.x; j0 < jend; j0 += 256 * U) {
-            T x[U][NS], z[U][NT];
+            const T *xp = X + bx + __ldg(tx + j);
+            const T *zp = Z + bz + __ldg(tz + j);
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                int j = j0 + u * 256;
-                bool on = j < jend;
-                int jj = on ? j : 0;
-                int ox = __ldg(tx + jj), oz = __ldg(tz + jj);
-#pragma unroll
-                for (int s = 0; s < NS; ++s)
-                    x[u][s] = (on && (NS == 1 || s < d.ns)) ? X[ox + d.xoff[s]] : T(0);
-#pragma unroll
-                for (int t = 0; t < NT; ++t)
-                    z[u][t] = (on && (NT == 1 || t < d.nt)) ? Z[oz + d.zoff[t]] : T(0);
+            for (int s = 0; s < NS; ++s) {
+                if (s0 + s < d.ns) cp_async_el(sb + s * 256, xp + d.xoff[s0 + s]);
+                else sb[s * 256] = T(0);
             }
 #pragma unroll
-            for (int u = 0; u < U; ++u)
+            for (int t = 0; t < NT; ++t) {
+                if (z0 + t < d.nt) cp_async_el(sb + (NS + t) * 256, zp + d.zoff[z0 + t]);
+                else sb[(NS + t) * 256] = T(0);
+            }
+        } else {
 #pragma unroll
-                for (int s = 0; s < NS; ++s)
-#pragma unroll
-                    for (int t = 0; t < NT; ++t) acc[s][t] += x[u][s] * z[u][t];
+            for (int w = 0; w < W; ++w) sb[w * 256] = T(0);
         }
+    };
+#pragma unroll
+    for (int k = 0; k < S - 1; ++k) {
+        if (k < nk) issue(k);
+        cp_async_commit();
     }
+    for (int k = 0; k < nk; ++k) {
+        if (k + S - 1 < nk) issue(k + S - 1);
+        cp_async_commit();
+        cp_async_wait<S - 1>();
+        const T *sb = buf + (k % S) * W * 256;
+        T x[NS], z[NT];
+#pragma unroll
+        for (int s = 0; s < NS; ++s) x[s] = sb[s * 256];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) z[t] = sb[(NS + t) * 256];
+#pragma unroll
+        for (int s = 0; s < NS; ++s)
+#pragma unroll
+            for (int t = 0; t < NT; ++t) acc[s][t] += x[s] * z[t];
+    }
+    cp_async_wait<0>();
+    // per-warp sums (a warp lies inside one sub-block), then per sub-block
     __shared__ T red[8][NS * NT];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -394,13 +460,13 @@ __global__ void __launch_bounds__(256) k_reduce_part(const __grid_constant__ RDe
             if (lane == 0) red[w][s * NT + t] = v;
         }
     __syncthreads();
-    for (int i = threadIdx.x; i < NS * NT; i += blockDim.x) {
+    const int wper = pp / 32;
+    for (int i = threadIdx.x; i < nb * NS * NT; i += blockDim.x) {
+        const int b = i / (NS * NT), ii = i - b * (NS * NT);
         T v = 0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) v += red[q][i];
-        part[(g * nchunks + blockIdx.x) * (8 * 8) + i] = v * (sx * sz);
+        for (int q = 0; q < wper; ++q) v += red[b * wper + q][ii];
+        part[(g * nchunks + blockIdx.x) * pstride + i] = v * (sx * sz);
     }
-    // the group's last block to finish sums the chunk partials (fixed order:
-    // lane-strided chunks, then a shuffle tree), writes O and its maximum
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(d.cnt + g, 1u) == (unsigned)(nchunks - 1);
@@ -410,11 +476,12 @@ __global__ void __launch_bounds__(256) k_reduce_part(const __grid_constant__ RDe
     T mx = 0;
     int64_t ox = 0, oz = 0, oo = beta * d.bso;
     group_offsets(d, gi, ox, oz, oo);
-    for (int i = w; i < NS * NT; i += (int)(blockDim.x >> 5)) {
-        const int s = i / NT, t = i - (i / NT) * NT;
+    for (int i = w; i < nb * NS * NT; i += (int)(blockDim.x >> 5)) {
+        const int b = i / (NS * NT), ii = i - b * (NS * NT);
+        const int s = (b / nbt) * NS + ii / NT, t = (b % nbt) * NT + ii % NT;
         if (s >= d.ns || t >= d.nt) continue;
         T v = 0;
-        for (int c = lane; c < nchunks; c += 32) v += __ldcg(part + (g * nchunks + c) * (8 * 8) + i);
+        for (int c = lane; c < nchunks; c += 32) v += __ldcg(part + (g * nchunks + c) * pstride + i);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0) {
@@ -426,74 +493,97 @@ __global__ void __launch_bounds__(256) k_reduce_part(const __grid_constant__ RDe
     if (threadIdx.x == 0) d.cnt[g] = 0u;
 }
 
-static void reduce_shape(const RDesc &d, int64_t &chunk, int &nchunks) {
-    int64_t groups = d.ng * d.nbeta;
-    int64_t ntile = d.nouter * ((d.nin + 1023) / 1024);
-    int64_t want = std::max<int64_t>(1, (152LL * 4) / std::max<int64_t>(1, groups));
-    chunk = std::max<int64_t>(1, (ntile + want - 1) / want);
-    nchunks = (int)((ntile + chunk - 1) / chunk);
+static int pow2ceil_i(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// One launch's shape: per-thread sub-block NS x NT (<= 8 x 8), nbs x nbt
+// sub-blocks (<= 8), the s range it covers, the chunking of the tiles.
+struct RedPiece {
+    int NS, NT, nbs, nbt, s0, ns;
+    int64_t chunk;
+    int nchunks, pstride;
+};
+
+static std::vector<RedPiece> reduce_pieces(const RDesc &d) {
+    std::vector<RedPiece> out;
+    RedPiece p{};
+    p.NS = d.ns <= 1 ? 1 : d.ns <= 2 ? 2 : d.ns <= 4 ? 4 : 8;
+    p.NT = d.nt <= 1 ? 1 : d.nt <= 2 ? 2 : d.nt <= 4 ? 4 : 8;
+    p.nbt = pow2ceil_i((d.nt + p.NT - 1) / p.NT);
+    int nbs_all = pow2ceil_i((d.ns + p.NS - 1) / p.NS);
+    p.nbs = std::min(nbs_all, 8 / p.nbt);
+    const int pp = 256 / (p.nbs * p.nbt);
+    const int64_t groups = d.ng * d.nbeta;
+    const int64_t ntile = d.nouter * ((d.nin + pp - 1) / pp);
+    // about two resident blocks per SM in total
+    const int64_t want = std::max<int64_t>(1, (152LL * 2) / std::max<int64_t>(1, groups));
+    p.chunk = std::max<int64_t>(1, (ntile + want - 1) / want);
+    p.nchunks = (int)((ntile + p.chunk - 1) / p.chunk);
+    p.pstride = p.nbs * p.nbt * p.NS * p.NT;
+    for (int s0 = 0; s0 < d.ns; s0 += p.nbs * p.NS) {
+        p.s0 = s0;
+        p.ns = std::min(p.nbs * p.NS, d.ns - s0);
+        out.push_back(p);
+    }
+    return out;
 }
 
 #ifdef TN_STREAM_HOST_DEFS
 size_t reduce_scratch_bytes(const RDesc &d, int elem_bytes) {
-    int64_t chunk;
-    int nchunks;
-    reduce_shape(d, chunk, nchunks);
-    return (size_t)(d.ng * d.nbeta * nchunks * 64) * elem_bytes;
+    size_t mx = 0;
+    for (auto &p : reduce_pieces(d))
+        mx = std::max(mx, (size_t)(d.ng * d.nbeta * p.nchunks) * p.pstride * elem_bytes);
+    return mx;
 }
 #endif
 
 template <typename T, int NS, int NT>
-static void reduce_go(const RDesc &d, void *scratch, cudaStream_t st) {
-    int64_t chunk;
-    int nchunks;
-    reduce_shape(d, chunk, nchunks);
-    int64_t groups = d.ng * d.nbeta;
-    dim3 grid((unsigned)nchunks, (unsigned)std::min<int64_t>(groups, 65535),
+static void reduce_go(const RDesc &d, const RedPiece &p, void *scratch, cudaStream_t st) {
+    const int64_t groups = d.ng * d.nbeta;
+    dim3 grid((unsigned)p.nchunks, (unsigned)std::min<int64_t>(groups, 65535),
               (unsigned)((groups + 65534) / 65535));
-    k_reduce_part<T, NS, NT><<<grid, 256, 0, st>>>(d, chunk, nchunks, (T *)scratch);
+    constexpr size_t smem = (size_t)red_stages<T>() * (NS + NT) * 256 * sizeof(T);
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(k_reduce_part<T, NS, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    });
+    k_reduce_part<T, NS, NT><<<grid, 256, smem, st>>>(d, p.nbs, p.nbt, p.chunk, p.nchunks,
+                                                      p.pstride, (T *)scratch);
 }
 
 template <typename T, int NS>
-static void reduce_nt(const RDesc &d, void *scratch, cudaStream_t st) {
-    if (d.nt <= 1) reduce_go<T, NS, 1>(d, scratch, st);
-    else if (d.nt <= 2) reduce_go<T, NS, 2>(d, scratch, st);
-    else if (d.nt <= 4) reduce_go<T, NS, 4>(d, scratch, st);
-    else reduce_go<T, NS, 8>(d, scratch, st);
+static void reduce_nt(const RDesc &d, const RedPiece &p, void *scratch, cudaStream_t st) {
+    if (p.NT == 1) reduce_go<T, NS, 1>(d, p, scratch, st);
+    else if (p.NT == 2) reduce_go<T, NS, 2>(d, p, scratch, st);
+    else if (p.NT == 4) reduce_go<T, NS, 4>(d, p, scratch, st);
+    else reduce_go<T, NS, 8>(d, p, scratch, st);
 }
 
-template <typename T>
-static void reduce_one(const RDesc &d, void *scratch, cudaStream_t st) {
-    if (d.ns <= 1) reduce_nt<T, 1>(d, scratch, st);
-    else if (d.ns <= 2) reduce_nt<T, 2>(d, scratch, st);
-    else if (d.ns <= 4) reduce_nt<T, 4>(d, scratch, st);
-    else reduce_nt<T, 8>(d, scratch, st);
-}
-
-// Outputs with more than 8 x 8 (s, t) combinations run as several launches
-// over 8 x 8 chunks of them (each re-reads only the operand slices it uses).
+// Outputs with more than 8 sub-blocks run as several launches over ranges of
+// s (each reads its slice of X and all of Z).
 template <typename T>
 void launch_reduce(const RDesc &d, void *scratch, cudaStream_t st) {
     if (d.ng * d.nbeta == 0) return;
-    for (int s0 = 0; s0 < d.ns; s0 += 8)
-        for (int t0 = 0; t0 < d.nt; t0 += 8) {
-            RDesc c = d;
-            c.ns = std::min(8, d.ns - s0);
-            c.nt = std::min(8, d.nt - t0);
-            for (int i = 0; i < c.ns; ++i) {
-                c.xoff[i] = d.xoff[s0 + i];
-                c.oso[i] = d.oso[s0 + i];
-            }
-            for (int i = 0; i < c.nt; ++i) {
-                c.zoff[i] = d.zoff[t0 + i];
-                c.oto[i] = d.oto[t0 + i];
-            }
-            reduce_one<T>(c, scratch, st);
+    for (const RedPiece &p : reduce_pieces(d)) {
+        RDesc c = d;
+        c.ns = p.ns;
+        for (int i = 0; i < c.ns; ++i) {
+            c.xoff[i] = d.xoff[p.s0 + i];
+            c.oso[i] = d.oso[p.s0 + i];
         }
+        if (p.NS == 1) reduce_nt<T, 1>(c, p, scratch, st);
+        else if (p.NS == 2) reduce_nt<T, 2>(c, p, scratch, st);
+        else if (p.NS == 4) reduce_nt<T, 4>(c, p, scratch, st);
+        else reduce_nt<T, 8>(c, p, scratch, st);
+    }
 }
 
 #ifdef TN_STREAM_HOST_DEFS
-int reduce_launches(const RDesc &d) { return ((d.ns + 7) / 8) * ((d.nt + 7) / 8); }
+int reduce_launches(const RDesc &d) { return (int)reduce_pieces(d).size(); }
 #endif
 
 
