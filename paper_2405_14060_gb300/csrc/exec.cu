@@ -1579,14 +1579,33 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
     return TN_OK;
 }
 
-// Per-class device time accumulated by a profiling run.
+// Per-class device time accumulated by a profiling run.  Every launch is
+// bracketed by a pair of events recorded back to back on the stream (no host
+// synchronisation between launches, so the device runs them as in a graph
+// replay); the durations are read once the run has finished.
 struct Prof {
     double ms[C_NCLS] = {0};
     double n[C_NCLS] = {0};
     double flops[C_NCLS] = {0};
     double bytes[C_NCLS] = {0};
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    std::vector<double> rec;   // per launch: class, ms, flops, bytes
+    std::vector<cudaEvent_t> ev;     // start, end per launch
+    std::vector<double> meta;        // per launch: class, flops, bytes
+    std::vector<double> rec;         // per launch: class, ms, flops, bytes
+    ~Prof() {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
+    void finish() {
+        for (size_t i = 0; i < meta.size() / 3; ++i) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, ev[2 * i], ev[2 * i + 1]);
+            int cls = (int)meta[3 * i];
+            this->ms[cls] += ms;
+            n[cls] += 1;
+            flops[cls] += meta[3 * i + 1];
+            bytes[cls] += meta[3 * i + 2];
+            rec.insert(rec.end(), {(double)cls, (double)ms, meta[3 * i + 1], meta[3 * i + 2]});
+        }
+    }
 };
 
 template <typename F>
@@ -1595,17 +1614,15 @@ static void timed(Prof *pr, cudaStream_t st, int cls, double flops, double bytes
         f();
         return;
     }
-    cudaEventRecord(pr->e0, st);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    pr->ev.push_back(e0);
+    pr->ev.push_back(e1);
+    cudaEventRecord(e0, st);
     f();
-    cudaEventRecord(pr->e1, st);
-    cudaEventSynchronize(pr->e1);
-    float ms = 0;
-    cudaEventElapsedTime(&ms, pr->e0, pr->e1);
-    pr->ms[cls] += ms;
-    pr->n[cls] += 1;
-    pr->rec.insert(pr->rec.end(), {(double)cls, (double)ms, flops, bytes});
-    pr->flops[cls] += flops;
-    pr->bytes[cls] += bytes;
+    cudaEventRecord(e1, st);
+    pr->meta.insert(pr->meta.end(), {(double)cls, flops, bytes});
 }
 
 template <typename T>
@@ -2666,15 +2683,12 @@ static tn_status profile_impl(tn_model *m, int task, int batch, const int32_t *e
         else CK(cudaMemset(P->d_evid, 0xff, eb));
     }
     Prof pr;
-    CK(cudaEventCreate(&pr.e0));
-    CK(cudaEventCreate(&pr.e1));
     for (int r = 0; r < reps; ++r) {
         if (P->dtype == 0) enqueue_program<double>(m, *P, st, &pr);
         else enqueue_program<float>(m, *P, st, &pr);
     }
     CK(cudaStreamSynchronize(st));
-    cudaEventDestroy(pr.e0);
-    cudaEventDestroy(pr.e1);
+    pr.finish();
     if (steps && nsteps) {
         int n = (int)(pr.rec.size() / 4);
         *nsteps = n;
