@@ -111,8 +111,10 @@ void tn_free_model(tn_model *m);
  * 2^24 assignments) and the results are combined on the device: log-sum-exp
  * of log Z for PR, Z-weighted marginals for MAR (a sliced variable's
  * marginal is the Z-share of its values).  Slicing bounds the largest
- * intermediate by the product of the sliced domains; MPE, MMAP and sampling
- * reject a sliced tree (TN_E_UNSUPPORTED).  tn_tree_stats then reports the
+ * intermediate by the product of the sliced domains; sampling draws the
+ * assignment of the sliced variables first (probability Z_a / Z, a second
+ * forward pass per drawn assignment); MPE and MMAP reject a sliced tree
+ * (TN_E_UNSUPPORTED).  tn_tree_stats then reports the
  * per-slice space complexity and the total time over all slices.
  * Errors: TN_E_ORDER (a malformed tree), TN_E_ARG (bad slice variables).
  */
@@ -152,6 +154,18 @@ tn_status tn_optimize_order(const tn_model *m, int method, int restarts, uint64_
  * tree.  The result is unchanged where no run pays off. */
 tn_status tn_reassociate(const tn_model *m, const int *left, const int *right,
                          int *left_out, int *right_out);
+
+/* Slice variables for a tree (left/right as tn_set_order's; NULL: the current
+ * tree): greedily adds the label of the current largest intermediate whose
+ * slicing gives the smallest space complexity (ties: the smallest total
+ * multiply-add count over all slices) until the per-slice space complexity
+ * is at most target_sc_log2 (log2 entries) or max_vars variables are chosen
+ * (slicing, Sec. Tensor networks: fixing a label splits the contraction into
+ * independent ones, one per value).  Writes at most max_vars variables to
+ * vars and their count to *nvars_out; pass them to tn_set_order.  Host only.
+ * Errors: TN_E_ARG (NULL outputs), TN_E_ORDER (an invalid tree). */
+tn_status tn_choose_slices(const tn_model *m, const int *left, const int *right,
+                           double target_sc_log2, int max_vars, int *vars, int *nvars_out);
 
 /* Complexities of the current tree for `batch` evidence sets:
  * out[0] = log2 of the total multiply-add count (time complexity, paper:

@@ -13,6 +13,7 @@
 #include <map>
 #include <memory>
 #include <numeric>
+#include <random>
 #include <set>
 #include <string>
 #include <tuple>
@@ -2101,6 +2102,71 @@ tn_status tn_optimize_order(const tn_model *m, int method, int restarts, uint64_
     return TN_OK;
 }
 
+tn_status tn_choose_slices(const tn_model *m, const int *left, const int *right,
+                           double target_sc_log2, int max_vars, int *vars, int *nvars_out) {
+    if (!m || !vars || !nvars_out || max_vars < 0) return fail(TN_E_ARG, "bad argument");
+    Tree t;
+    if (left && right) {
+        t.nleaves = (int)model_net(m->md, false).leaf.size();
+        t.left.assign(left, left + t.nleaves - 1);
+        t.right.assign(right, right + t.nleaves - 1);
+        std::string err = validate_tree(t);
+        if (!err.empty()) return fail(TN_E_ORDER, err);
+    } else {
+        t = m->has_tree ? m->tree : greedy_tree(model_net(m->md, false));
+    }
+    // sc (log2 entries of the largest intermediate), tc (log2 multiply-adds
+    // over all slices) and the largest node of the tree with `sl` sliced
+    auto cost = [&](const std::vector<int> &sl, double &sc, double &tc, int &big) {
+        Plan p;
+        build_plan(model_net(m->md, false, sl), t, p);
+        double nass = 1;
+        for (int v : sl) nass *= m->md.card[v];
+        sc = 0;
+        tc = 0;
+        big = -1;
+        const int n = t.nleaves;
+        for (int id = n; id < 2 * n - 1; ++id) {
+            double e = std::log2((double)p.node[id].size);
+            if (e > sc) {
+                sc = e;
+                big = id;
+            }
+            tc += p.node[id].muladds;
+        }
+        tc = std::log2(std::max(1.0, tc * nass));
+        return p;
+    };
+    std::vector<int> sl;
+    double sc, tc;
+    int big;
+    Plan p = cost(sl, sc, tc, big);
+    while ((int)sl.size() < max_vars && sc > target_sc_log2 && big >= 0) {
+        // candidates: the labels of the current largest intermediate
+        Labels cand = p.node[big].labels;
+        int bestv = -1;
+        double bsc = 0, btc = 0;
+        for (int v : cand) {
+            std::vector<int> trial = sl;
+            trial.push_back(v);
+            double s2, t2;
+            int b2;
+            cost(trial, s2, t2, b2);
+            if (bestv < 0 || s2 < bsc || (s2 == bsc && t2 < btc)) {
+                bestv = v;
+                bsc = s2;
+                btc = t2;
+            }
+        }
+        if (bestv < 0) break;
+        sl.push_back(bestv);
+        p = cost(sl, sc, tc, big);
+    }
+    std::copy(sl.begin(), sl.end(), vars);
+    *nvars_out = (int)sl.size();
+    return TN_OK;
+}
+
 tn_status tn_reassociate(const tn_model *m, const int *left, const int *right, int *left_out,
                          int *right_out) {
     if (!m || !left || !right || !left_out || !right_out) return fail(TN_E_ARG, "NULL argument");
@@ -2287,11 +2353,39 @@ tn_status tn_map(tn_model *m, const int32_t *evid, const tn_options *opts, int32
     return TN_OK;
 }
 
+// Draw n samples into d_out from the program's cached forward tensors (the
+// last run), with the Philox key `seed`.
+static tn_status draw_samples(tn_model *m, Program &P, int64_t n, uint64_t seed, int8_t *d_out,
+                              cudaStream_t st) {
+    if (n == 0) return TN_OK;
+    int64_t coff = 0;
+    for (auto &c : P.cdf_nodes) {
+        // cumulative tables of the nodes with large summed spaces
+        if (P.dtype == 0) launch_cdf_rows<double>(c.first, c.second, P.cdf + coff, st);
+        else launch_cdf_rows<float>(c.first, c.second, P.cdf + coff, st);
+        coff += c.second * c.first.ktotal;
+    }
+    if (P.dtype == 0)
+        launch_sample<double>(P.d_meta, P.nmeta, (const double *)P.arena, P.cdf, P.d_evid,
+                              m->md.nvars, n, seed, d_out, st);
+    else
+        launch_sample<float>(P.d_meta, P.nmeta, (const float *)P.arena, P.cdf, P.d_evid,
+                             m->md.nvars, n, seed, d_out, st);
+    CK(cudaGetLastError());
+    return TN_OK;
+}
+
+static uint64_t mix64(uint64_t x) {
+    // SplitMix64 finaliser (Steele, Lea, Flood 2014)
+    x += 0x9e3779b97f4a7c15ull;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+}
+
 tn_status tn_sample(tn_model *m, const int32_t *evid, uint64_t seed, int64_t n,
                     const tn_options *opts, int8_t *samples) {
     if (!m || n < 0 || (!samples && n)) return fail(TN_E_ARG, "bad argument");
-    if (!m->slice_vars.empty())
-        return fail(TN_E_UNSUPPORTED, "this task does not run on a sliced tree; set the order without slices");
     for (int v = 0; v < m->md.nvars; ++v)
         if (m->md.card[v] > 127) return fail(TN_E_UNSUPPORTED, "domain size above 127");
     tn_status s = check_evid(m, 1, evid);
@@ -2302,39 +2396,121 @@ tn_status tn_sample(tn_model *m, const int32_t *evid, uint64_t seed, int64_t n,
     cudaStream_t st = stream_of(m, opts);
     s = override_tables(m, nullptr, 0, st);
     if (s) return s;
-    s = run_program(m, *P, evid, false, st);
-    if (s) return s;
-    double lz;
-    CK(cudaMemcpy(&lz, P->d_logz, 8, cudaMemcpyDeviceToHost));
-    if (!(lz > -INFINITY)) return fail(TN_E_ARG, "p(e) = 0");
-    if (n == 0) return TN_OK;
-    int8_t *d_out = nullptr;
-    CK(cudaMallocAsync(&d_out, (size_t)n * m->md.nvars, st));
-    CK(cudaEventRecord(m->ev0, st));
-    {
-        // cumulative tables of the nodes with large summed spaces
-        int64_t coff = 0;
-        for (auto &c : P->cdf_nodes) {
-            if (P->dtype == 0) launch_cdf_rows<double>(c.first, c.second, P->cdf + coff, st);
-            else launch_cdf_rows<float>(c.first, c.second, P->cdf + coff, st);
-            coff += c.second * c.first.ktotal;
-        }
+    const int nv = m->md.nvars;
+    if (m->slice_vars.empty()) {
+        s = run_program(m, *P, evid, false, st);
+        if (s) return s;
+        double lz;
+        CK(cudaMemcpy(&lz, P->d_logz, 8, cudaMemcpyDeviceToHost));
+        if (!(lz > -INFINITY)) return fail(TN_E_ARG, "p(e) = 0");
+        if (n == 0) return TN_OK;
+        int8_t *d_out = nullptr;
+        CK(cudaMallocAsync(&d_out, (size_t)n * nv, st));
+        CK(cudaEventRecord(m->ev0, st));
+        s = draw_samples(m, *P, n, seed, d_out, st);
+        if (s) return s;
+        CK(cudaEventRecord(m->ev1, st));
+        CK(cudaMemcpyAsync(samples, d_out, (size_t)n * nv, cudaMemcpyDeviceToHost, st));
+        CK(cudaFreeAsync(d_out, st));
+        CK(cudaStreamSynchronize(st));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, m->ev0, m->ev1));
+        m->last_ms += ms;
+        CK(cudaGetLastError());
+        return TN_OK;
     }
-    if (P->dtype == 0)
-        launch_sample<double>(P->d_meta, P->nmeta, (const double *)P->arena, P->cdf, P->d_evid,
-                              m->md.nvars, n, seed, d_out, st);
-    else
-        launch_sample<float>(P->d_meta, P->nmeta, (const float *)P->arena, P->cdf, P->d_evid,
-                             m->md.nvars, n, seed, d_out, st);
-    CK(cudaEventRecord(m->ev1, st));
-    CK(cudaMemcpyAsync(samples, d_out, (size_t)n * m->md.nvars, cudaMemcpyDeviceToHost, st));
+    // Sliced tree: p(x) = sum_a p(a) p(x | a) with p(a) = Z_a / Z over the
+    // assignments a of the sliced variables.  Pass 1 computes every Z_a, the
+    // number of samples per assignment is drawn from the multinomial, pass 2
+    // re-runs each drawn assignment's forward pass (its tensors are the
+    // cache) and samples within it; the rows are shuffled at the end.
+    int64_t nass;
+    s = slice_setup(m, nass);
+    if (s) return s;
+    const int nsl = (int)m->slice_vars.size();
+    std::vector<int32_t> ev(nv, -1);
+    if (evid) std::copy(evid, evid + nv, ev.begin());
+    double tms = 0;
+    // forward pass of assignment a; `possible` false when the evidence rules it out
+    auto run_assignment = [&](int64_t a, bool &possible) -> tn_status {
+        std::vector<int32_t> ea = ev;
+        int64_t r = a;
+        possible = true;
+        for (int j = nsl - 1; j >= 0; --j) {
+            const int v = m->slice_vars[j], c = m->md.card[v];
+            const int32_t val = (int32_t)(r % c);
+            r /= c;
+            if (ea[v] >= 0 && ea[v] != val) possible = false;
+            ea[v] = val;
+        }
+        if (!possible) return TN_OK;
+        CK(cudaMemcpyAsync(P->d_slice_val, m->d_sl_tab + a * nsl, (size_t)nsl * 4,
+                           cudaMemcpyDeviceToDevice, st));
+        tn_status e = run_program(m, *P, ea.data(), false, st);
+        tms += m->last_ms;
+        return e;
+    };
+    std::vector<double> lz(nass, -INFINITY);
+    for (int64_t a = 0; a < nass; ++a) {
+        bool ok;
+        s = run_assignment(a, ok);
+        if (s) return s;
+        if (!ok) continue;
+        CK(cudaMemcpy(&lz[a], P->d_logz, 8, cudaMemcpyDeviceToHost));
+        if (!(lz[a] > -INFINITY)) lz[a] = -INFINITY;
+    }
+    double mx = -INFINITY;
+    for (double v : lz) mx = std::max(mx, v);
+    if (!(mx > -INFINITY)) return fail(TN_E_ARG, "p(e) = 0");
+    std::vector<double> cum(nass);
+    double acc = 0;
+    for (int64_t a = 0; a < nass; ++a) {
+        acc += lz[a] > -INFINITY ? std::exp(lz[a] - mx) : 0.0;
+        cum[a] = acc;
+    }
+    if (n == 0) return TN_OK;
+    std::mt19937_64 rng(mix64(seed ^ 0x5ca1ab1eull));
+    std::uniform_real_distribution<double> U(0.0, 1.0);
+    std::vector<int64_t> cnt(nass, 0);
+    for (int64_t i = 0; i < n; ++i) {
+        const double u = U(rng) * acc;
+        int64_t a = std::upper_bound(cum.begin(), cum.end(), u) - cum.begin();
+        cnt[std::min(a, nass - 1)]++;
+    }
+    int8_t *d_out = nullptr;
+    CK(cudaMallocAsync(&d_out, (size_t)n * nv, st));
+    int64_t off = 0;
+    for (int64_t a = 0; a < nass; ++a) {
+        if (!cnt[a]) continue;
+        bool ok;
+        s = run_assignment(a, ok);
+        if (s) return s;
+        CK(cudaEventRecord(m->ev0, st));
+        s = draw_samples(m, *P, cnt[a], mix64(seed + (uint64_t)a), d_out + off * nv, st);
+        if (s) return s;
+        CK(cudaEventRecord(m->ev1, st));
+        CK(cudaStreamSynchronize(st));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, m->ev0, m->ev1));
+        tms += ms;
+        off += cnt[a];
+    }
+    std::vector<int8_t> h((size_t)n * nv);
+    CK(cudaMemcpyAsync(h.data(), d_out, h.size(), cudaMemcpyDeviceToHost, st));
     CK(cudaFreeAsync(d_out, st));
     CK(cudaStreamSynchronize(st));
-    float ms = 0;
-    CK(cudaEventElapsedTime(&ms, m->ev0, m->ev1));
-    m->last_ms += ms;
+    // rows grouped by assignment -> a uniformly random order (Fisher-Yates)
+    std::vector<int64_t> perm(n);
+    for (int64_t i = 0; i < n; ++i) perm[i] = i;
+    for (int64_t i = n - 1; i > 0; --i) {
+        int64_t j = std::min(i, (int64_t)(U(rng) * (double)(i + 1)));
+        std::swap(perm[i], perm[j]);
+    }
+    for (int64_t i = 0; i < n; ++i)
+        std::copy(h.begin() + perm[i] * nv, h.begin() + (perm[i] + 1) * nv, samples + i * nv);
+    m->last_ms = tms;
     CK(cudaGetLastError());
-    return TN_OK;
+    return check_device_error(m);
 }
 
 // MMAP by the two-phase method of Sec. MMAP: (1) partition the factors so

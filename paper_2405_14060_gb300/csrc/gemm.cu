@@ -305,6 +305,7 @@ constexpr unsigned long long TC_WAIT_NS = 2000000000ull;
 
 struct TCParams {
     int64_t R, C, ldd, bsd;
+    int64_t ntn, ntm;           // column / row tiles (grid.x = batch x rows x columns)
     int kt;                     // number of 128-byte K slabs
     float *D;
     unsigned long long *mxd;
@@ -373,8 +374,11 @@ __global__ void __launch_bounds__(128, 1)
     uint64_t *bars = (uint64_t *)(sY + TC_STAGES * TC_YBYTES);
     uint32_t *tslot = (uint32_t *)(bars + 2 * TC_STAGES + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t n0 = (int64_t)blockIdx.x * TC_BN, m0 = (int64_t)blockIdx.y * TC_BM;
-    const int bz = blockIdx.z;
+    // one flat tile index (columns fastest) keeps every grid extent in range
+    const int64_t tl = blockIdx.x, per_b = p.ntn * p.ntm;
+    const int bz = (int)(tl / per_b);
+    const int64_t rem = tl - (int64_t)bz * per_b;
+    const int64_t n0 = (rem % p.ntn) * TC_BN, m0 = (rem / p.ntn) * TC_BM;
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + TC_STAGES),
                    tfull = smem_u32(bars + 2 * TC_STAGES);
     if (threadIdx.x == 0) {
@@ -537,7 +541,8 @@ bool tc_gemm_supported(const GDesc &g) {
     if (((uintptr_t)g.X | (uintptr_t)g.Y) & 15) return false;
     if ((g.ldx * es) % 16 || (g.ldy * es) % 16) return false;
     if (g.batch > 1 && ((g.bsx * es) % 16 || (g.bsy * es) % 16)) return false;
-    if (g.R > (1LL << 31) - TC_BM || g.C > (1LL << 31) - TC_BN || g.batch > 65535) return false;
+    if (g.R > (1LL << 31) - TC_BM || g.C > (1LL << 31) - TC_BN) return false;
+    if (((g.C + TC_BN - 1) / TC_BN) * ((g.R + TC_BM - 1) / TC_BM) * g.batch >= (1LL << 31)) return false;
     if (g.K < 1) return false;
     return encode_fn() != nullptr;
 }
@@ -579,8 +584,10 @@ cudaError_t launch_tc_gemm(const GDesc &g, int *err_flag, cudaStream_t st) {
     p.beta_div_batch = g.beta_div_batch;
     p.beta_div_row = g.beta_div_row;
     p.err = err_flag;
-    dim3 grid((unsigned)((g.C + TC_BN - 1) / TC_BN), (unsigned)((g.R + TC_BM - 1) / TC_BM),
-              (unsigned)g.batch);
+    p.ntn = (g.C + TC_BN - 1) / TC_BN;
+    p.ntm = (g.R + TC_BM - 1) / TC_BM;
+    if (p.ntn * p.ntm * g.batch >= (1LL << 31)) return cudaErrorInvalidConfiguration;
+    dim3 grid((unsigned)(p.ntn * p.ntm * g.batch), 1, 1);
     if (bf16) k_tc_gemm<1><<<grid, 128, TC_SMEM, st>>>(mx, my, p);
     else k_tc_gemm<0><<<grid, 128, TC_SMEM, st>>>(mx, my, p);
     return cudaGetLastError();
@@ -594,8 +601,10 @@ __global__ void __launch_bounds__(256) k_simt_gemm(const __grid_constant__ GDesc
     __shared__ T sx[BK][BM + 1];
     __shared__ T sy[BK][BN + 1];
     const int t = threadIdx.x, ty = t / 16, tx = t % 16;
-    const int64_t r0 = (int64_t)blockIdx.y * BM, c0 = (int64_t)blockIdx.x * BN;
-    const int64_t b = blockIdx.z;
+    // one flat tile index (columns fastest) keeps every grid extent in range
+    const int64_t ntn = (g.C + BN - 1) / BN, ntm = (g.R + BM - 1) / BM;
+    const int64_t b = (int64_t)blockIdx.x / (ntn * ntm), rem = (int64_t)blockIdx.x - b * ntn * ntm;
+    const int64_t r0 = (rem / ntn) * BM, c0 = (rem % ntn) * BN;
     const T *X = (const T *)g.X + b * g.bsx;
     const T *Y = (const T *)g.Y + b * g.bsy;
     T acc[4][4];
@@ -665,7 +674,7 @@ __global__ void __launch_bounds__(256) k_simt_gemm(const __grid_constant__ GDesc
 }
 
 void launch_simt_gemm(const GDesc &g, cudaStream_t st) {
-    dim3 grid((unsigned)((g.C + 63) / 64), (unsigned)((g.R + 63) / 64), (unsigned)g.batch);
+    dim3 grid((unsigned)(((g.C + 63) / 64) * ((g.R + 63) / 64) * g.batch), 1, 1);
     if (g.xtype == E_F64) k_simt_gemm<double><<<grid, 256, 0, st>>>(g);
     else k_simt_gemm<float><<<grid, 256, 0, st>>>(g);
 }

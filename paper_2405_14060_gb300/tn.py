@@ -24,7 +24,7 @@ EXPORTS = ["tn_load_model", "tn_load_model_arrays", "tn_free_model", "tn_set_ord
            "tn_mar", "tn_map", "tn_mmap", "tn_sample", "tn_pr_dev", "tn_mar_dev",
            "tn_last_device_ms", "tn_last_launch_count", "tn_last_error", "tn_contract_dev",
            "tn_profile", "tn_profile_steps", "tn_contract_dev_noalloc",
-           "tn_reassociate"]
+           "tn_reassociate", "tn_choose_slices"]
 PROFILE_CLASSES = ["small", "absorb", "reduce", "tcgemm", "simtgemm", "prep", "generic", "unused7"]
 
 
@@ -72,6 +72,8 @@ def lib():
             "tn_profile": [P, I, I, P, P, I, P],
             "tn_profile_steps": [P, I, I, P, P, I, P, P],
             "tn_contract_dev_noalloc": [I, P, I, P, P, I, P, P, I, P, P, I, I, P, P],
+            "tn_reassociate": [P, P, P, P, P],
+            "tn_choose_slices": [P, P, P, D, I, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -200,6 +202,20 @@ class Model:
         ro = np.zeros_like(r)
         _ck(lib().tn_reassociate(self._h, _ptr(l), _ptr(r), _ptr(lo), _ptr(ro)))
         return lo, ro
+
+    def choose_slices(self, target_sc_log2, max_vars=16, left=None, right=None):
+        """Variables to slice so that every slice's largest intermediate holds
+        at most 2**target_sc_log2 entries (greedy; at most max_vars)."""
+        out = np.zeros(max(1, max_vars), np.int32)
+        n = ctypes.c_int(0)
+        lp = rp = None
+        if left is not None:
+            l = np.ascontiguousarray(left, np.int32)
+            r = np.ascontiguousarray(right, np.int32)
+            lp, rp = _ptr(l), _ptr(r)
+        _ck(lib().tn_choose_slices(self._h, lp, rp, float(target_sc_log2), max_vars, _ptr(out),
+                                   ctypes.byref(n)))
+        return [int(v) for v in out[:n.value]]
 
     def tree_stats(self, batch=1, prec="fp64"):
         out = np.zeros(6)

@@ -452,3 +452,37 @@ def test_rrg3_sampling_statistics():
         exact = np.sum(joint * S[:, i] * S[:, j])
         empc = np.mean(Ss[:, i] * Ss[:, j])
         assert abs(empc - exact) < 5 * np.sqrt(max(1e-12, 1 - exact ** 2) / n) + 1e-4
+
+
+def test_sampling_on_sliced_tree():
+    """Sampling through a sliced tree (slice assignment drawn with
+    probability Z_a / Z, then backward sampling within it): per-spin
+    frequencies and edge correlations within 5 sigma of the exact values;
+    observed variables (one of them sliced) keep their values."""
+    m = synth.rrg3_ising(16, 33, field=True)
+    M = tn.Model.from_synth(m)
+    l, r = M.optimize_order(1, 4, 2)
+    M.set_order(l, r, slice_vars=[3, 9])
+    n = 100000
+    s = M.sample(n, seed=5, prec="fp32")
+    _, marg = oracle.ve_mar(m)
+    p1 = np.array([mv[1] for mv in marg])
+    emp = s.mean(axis=0)
+    assert np.all(np.abs(emp - p1) < 5 * np.sqrt(p1 * (1 - p1) / n) + 1e-4)
+    joint = oracle.brute_joint(m)
+    S = 2 * ((np.arange(len(joint))[:, None] >> np.arange(m.nvars)[::-1]) & 1) - 1
+    Ss = 2 * s.astype(np.int64) - 1
+    for sc in m.scopes:
+        if len(sc) == 2:
+            i, j = int(sc[0]), int(sc[1])
+            exact = np.sum(joint * S[:, i] * S[:, j])
+            tol = 5 * np.sqrt(max(1e-12, 1 - exact ** 2) / n) + 1e-4
+            assert abs(np.mean(Ss[:, i] * Ss[:, j]) - exact) < tol
+    ev = np.full(m.nvars, -1, np.int32)
+    ev[3], ev[5] = 1, 0
+    n2 = 20000
+    s2 = M.sample(n2, evid=ev, seed=6, prec="fp64")
+    assert np.all(s2[:, 3] == 1) and np.all(s2[:, 5] == 0)
+    _, marg_e = oracle.ve_mar(m, ev)
+    p1e = np.array([mv[1] for mv in marg_e])
+    assert np.all(np.abs(s2.mean(axis=0) - p1e) < 5 * np.sqrt(p1e * (1 - p1e) / n2) + 1e-4)

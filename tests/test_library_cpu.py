@@ -221,3 +221,25 @@ def test_reassociate_keeps_the_contraction_and_cuts_read_write():
         bad[-1] = bad[0]
         Ms.reassociate(bad, rs)
     assert e.value.status == 3
+
+
+def test_choose_slices_reaches_target():
+    """Greedy slice selection: the per-slice space complexity reaches the
+    target and slicing never increases the total multiply-add count by more
+    than the number of slices."""
+    m = synth.grid_ising(10, 4)
+    M = tn.Model.from_synth(m)
+    l, r = M.optimize_order(0)
+    M.set_order(l, r)
+    full = M.tree_stats()
+    sl = M.choose_slices(full["sc"] - 3, 8, l, r)
+    assert 1 <= len(sl) <= 8 and len(set(sl)) == len(sl)
+    M.set_order(l, r, slice_vars=sl)
+    st = M.tree_stats()
+    assert st["sc"] <= full["sc"] - 3
+    assert st["tc"] <= full["tc"] + len(sl) + 1e-9
+    # already at the target: nothing to slice
+    assert M.choose_slices(full["sc"], 8, l, r) == []
+    # the current tree is used when none is given
+    M.set_order(l, r)
+    assert M.choose_slices(full["sc"] - 3, 8) == sl
