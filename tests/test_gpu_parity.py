@@ -486,3 +486,30 @@ def test_sampling_on_sliced_tree():
     _, marg_e = oracle.ve_mar(m, ev)
     p1e = np.array([mv[1] for mv in marg_e])
     assert np.all(np.abs(s2.mean(axis=0) - p1e) < 5 * np.sqrt(p1e * (1 - p1e) / n2) + 1e-4)
+
+
+def test_workload5_sliced_pr_mar_and_sampling():
+    """Workload 5 at full size (240-spin random 3-regular graph, no fields):
+    annealed tree with re-associated chains, sliced to per-slice space 2^30
+    (16 slice assignments).  PR + MAR in TF32: log Z within 1e-4 relative of
+    the FP32 PR on the same tree; every marginal is 1/2 by the spin-flip
+    symmetry of a field-free Ising model; 100000 samples whose spin
+    frequencies are within 5 sigma of 1/2 and whose magnetisation per sample
+    has zero mean within 5 sigma."""
+    w = synth.workload(5)
+    m = w.model
+    M = tn.Model.from_synth(m)
+    l, r = M.reassociate(*M.optimize_order(2, 20, 1))
+    sl = M.choose_slices(30, 12, l, r)
+    M.set_order(l, r, slice_vars=sl)
+    assert M.tree_stats(1, "fp32")["sc"] <= 30
+    lz_t, mg_t = M.mar(prec="tf32")
+    lz_f = M.pr(prec="fp32")
+    assert abs(lz_t[0] - lz_f[0]) <= 1e-4 * abs(lz_f[0])
+    assert np.max(np.abs(mg_t - 0.5)) < 1e-3
+    n = 100000
+    s = M.sample(n, seed=7, prec="tf32")
+    freq = s.mean(axis=0)
+    assert np.all(np.abs(freq - 0.5) < 5 * np.sqrt(0.25 / n))
+    mag = (2 * s.astype(np.int64) - 1).sum(axis=1)
+    assert abs(mag.mean()) < 5 * mag.std() / np.sqrt(n)
