@@ -134,6 +134,7 @@ struct Step {
     ADesc ad;
     RDesc rd;
     double flops = 0, bytes = 0;   // algorithmic: 2 * multiply-adds; operands + result once
+    const char *why = "";          // why a strided contraction did not stream (plan trace)
 };
 
 struct Program {
@@ -589,6 +590,9 @@ static bool combo_offsets(const std::vector<int> &card, const Labels &labs, cons
     return true;
 }
 
+// Why the last make_absorb call declined (plan trace only).
+static const char *absorb_reject = "";
+
 // Absorb: X streamed once, W small; Y's labels = R (from X) + T (new).
 static bool make_absorb(const std::vector<int> &card, const Labels &lx, bool bx, int64_t perx,
                         const void *X, const unsigned long long *mxx, const Labels &lw, bool bw,
@@ -597,7 +601,7 @@ static bool make_absorb(const std::vector<int> &card, const Labels &lx, bool bx,
                         unsigned long long *mxy, const Labels *sorder, int nbeta,
                         int32_t *argmax, ADesc &d) {
     std::memset(&d, 0, sizeof d);
-    if (by != (bx || bw)) return false;
+    if (by != (bx || bw)) { absorb_reject = "batch label"; return false; }
     std::set<int> sx(lx.begin(), lx.end()), sw(lw.begin(), lw.end()), sy(ly.begin(), ly.end());
     Labels R, T, S;
     for (int v : ly) (sx.count(v) ? R : T).push_back(v);
@@ -608,13 +612,13 @@ static bool make_absorb(const std::vector<int> &card, const Labels &lx, bool bx,
         for (int v : lw)
             if (!sy.count(v) && !sx.count(v)) S.push_back(v);
     }
-    if (!combo_offsets(card, S, lx, sx, lw, sw, AMAX, d.ns, d.xoff, d.wso)) return false;
-    if (!combo_offsets(card, T, ly, sy, lw, sw, AMAX, d.nt, d.yoff, d.wto)) return false;
+    if (!combo_offsets(card, S, lx, sx, lw, sw, AMAX, d.ns, d.xoff, d.wso)) { absorb_reject = "summed combinations"; return false; }
+    if (!combo_offsets(card, T, ly, sy, lw, sw, AMAX, d.nt, d.yoff, d.wto)) { absorb_reject = "new combinations"; return false; }
     {
         int ps = 1, pt = 1;
         while (ps < d.ns) ps <<= 1;
         while (pt < d.nt) pt <<= 1;
-        if (ps * pt > 256) return false;
+        if (ps * pt > 256) { absorb_reject = "combination product"; return false; }
     }
     std::vector<SDim> raw;
     for (int v : R)
@@ -647,7 +651,7 @@ static bool make_absorb(const std::vector<int> &card, const Labels &lx, bool bx,
             break;
         }
     }
-    if ((int)f.size() > MAXD) return false;
+    if ((int)f.size() > MAXD) { absorb_reject = "too many dims"; return false; }
     d.nrd = (int)f.size();
     d.nr = 1;
     bool p2 = true;
@@ -675,7 +679,7 @@ static bool make_absorb(const std::vector<int> &card, const Labels &lx, bool bx,
         ew += (f[i].sz - 1) * f[i].s2;
         d.nin *= f[i].sz;
     }
-    if (ex >= (1LL << 31) || ey >= (1LL << 31) || ew >= (1LL << 31)) return false;
+    if (ex >= (1LL << 31) || ey >= (1LL << 31) || ew >= (1LL << 31)) { absorb_reject = "32-bit inner offsets"; return false; }
     d.nouter = d.nr / d.nin;
     // shared-label combinations (R dims that W holds), mixed radix, last fastest
     {
@@ -683,7 +687,7 @@ static bool make_absorb(const std::vector<int> &card, const Labels &lx, bool bx,
         for (int i = d.nrd - 1; i >= 0; --i) {
             d.rshc[i] = f[i].s2 ? (int32_t)c : 0;
             if (f[i].s2) c *= f[i].sz;
-            if (c >= (1LL << 30)) return false;
+            if (c >= (1LL << 30)) { absorb_reject = "shared combinations"; return false; }
         }
         d.nsh = (int)c;
     }
@@ -941,8 +945,8 @@ static void trace_program(const Program &P) {
                 if (st.g.has_post) pd("post", st.g.post);
             }
             else
-                fprintf(stderr, "%s %d contract outs %lld k %lld", dir, i, (long long)st.d.nout_total,
-                        (long long)st.d.ktotal);
+                fprintf(stderr, "%s %d contract outs %lld k %lld [%s]", dir, i,
+                        (long long)st.d.nout_total, (long long)st.d.ktotal, st.why);
             fprintf(stderr, " MB %.3f MFLOP %.3f\n", st.bytes / 1e6, st.flops / 1e6);
             ++i;
         }
@@ -1205,11 +1209,13 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
             st.flops = flops;
             st.bytes = bytes;
             const Node &na = pl.node[nd.a], &nb = pl.node[nd.b];
+            absorb_reject = "";
             if (make_absorb(net.card, na.labels, na.beta, P.fwd[nd.a].per, fptr(nd.a),
                             mxp(P.fwd[nd.a].mx), nb.labels, nb.beta, P.fwd[nd.b].per, fptr(nd.b),
                             mxp(P.fwd[nd.b].mx), nd.labels, nd.beta, P.fwd[id].per, fptr(id),
                             mxp(P.fwd[id].mx), &nd.elim, nbeta,
                             maxplus ? P.am + P.am_off[id] : nullptr, st.ad) ||
+                ((st.why = absorb_reject), false) ||
                 make_absorb(net.card, nb.labels, nb.beta, P.fwd[nd.b].per, fptr(nd.b),
                             mxp(P.fwd[nd.b].mx), na.labels, na.beta, P.fwd[nd.a].per, fptr(nd.a),
                             mxp(P.fwd[nd.a].mx), nd.labels, nd.beta, P.fwd[id].per, fptr(id),
@@ -1289,6 +1295,7 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                                     st.d);
                     if (!err.empty()) return fail(TN_E_UNSUPPORTED, err);
                     st.kind = 0;
+                    st.why = absorb_reject;
                     scratch = std::max(scratch, contract_scratch_bytes(st.d, P.esz));
                 }
                 P.bsteps.push_back(st);
@@ -1325,6 +1332,7 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                                     st.d);
                     if (!err.empty()) return fail(TN_E_UNSUPPORTED, err);
                     st.kind = 0;
+                    st.why = absorb_reject;
                     scratch = std::max(scratch, contract_scratch_bytes(st.d, P.esz));
                 }
                 P.bsteps.push_back(st);
