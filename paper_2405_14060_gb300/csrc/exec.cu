@@ -7,6 +7,7 @@
 // launches are captured once into a CUDA graph and replayed on every call, so
 // a call costs one graph launch plus the copies of its inputs and outputs.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -135,6 +136,11 @@ struct Step {
     RDesc rd;
     double flops = 0, bytes = 0;   // algorithmic: 2 * multiply-adds; operands + result once
     const char *why = "";          // why a strided contraction did not stream (plan trace)
+    int node = -1;                 // the tensor this step writes: fwd[node] or adj[node]
+    bool adjoint = false;
+    int lane = 0;                  // stream of the step inside the program's graph
+    std::vector<int> waits;        // events (other lanes' results) to wait for first
+    int rec = -1;                  // event to record after the step (-1: none)
 };
 
 struct Program {
@@ -183,8 +189,15 @@ struct Program {
     cudaGraphExec_t gexec = nullptr;
     int launches = 0;
     int64_t marg_stride = 0, grad_stride = 0;
+    // independent subtrees on separate streams (lanes) of the captured graph
+    int nlanes = 1;
+    std::vector<int> lane;                     // per tree node
+    std::vector<void *> lscratch;              // per lane: reduce / split-K scratch
+    std::vector<unsigned int *> lrcnt;         // per lane: reduce completion counters
+    std::vector<cudaEvent_t> ev;               // 2 NN + 2 + nlanes events (capture only)
     ~Program() {
         if (gexec) cudaGraphExecDestroy(gexec);
+        for (auto e : ev) cudaEventDestroy(e);
     }
 };
 
@@ -206,6 +219,7 @@ struct tn_model {
     bool tables_overridden = false;
     int device = -1;
     cudaStream_t stream = nullptr;
+    std::vector<cudaStream_t> lanes;   // extra streams that graph capture forks onto
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::map<std::tuple<int, int, int, int>, std::unique_ptr<Program>> progs;
     double last_ms = 0;
@@ -220,6 +234,7 @@ struct tn_model {
         if (d_err) cudaFree(d_err);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
+        for (auto l : lanes) cudaStreamDestroy(l);
         if (stream) cudaStreamDestroy(stream);
     }
 };
@@ -1055,28 +1070,69 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
         if (!P.micro[id]) bwd_order.push_back(id);
     for (auto &kv : msub)
         for (auto it = kv.second.rbegin(); it != kv.second.rend(); ++it) bwd_order.push_back(*it);
-    OffsetAlloc A;
-    for (int id = 0; id < n; ++id) P.fwd[id].off = A.alloc(P.fwd[id].elems);
-    // Micro subtrees run concurrently (one CTA each), so memory is never
-    // recycled inside the micro phase; their tensors are tiny.
-    for (int id : fwd_order) {
-        const Node &nd = pl.node[id];
-        P.fwd[id].off = A.alloc(P.fwd[id].elems);
-        if (!keep_all && !P.micro[id]) {
-            A.release(P.fwd[nd.a].off, P.fwd[nd.a].elems);
-            A.release(P.fwd[nd.b].off, P.fwd[nd.b].elems);
-        }
-    }
-    if (backward) {
-        P.adj[pl.root].off = A.alloc(P.adj[pl.root].elems);
-        for (int id : bwd_order) {
+    // ---- lanes: in PR and MAR programs the lighter child subtree of a node,
+    // when it carries at least 3% of the tree's tensor entries, runs on
+    // another stream of the captured graph (its steps wait for the results
+    // they read through events), so independent parts of the tree overlap.
+    // Memory is then never recycled, as concurrent parts would race on it.
+    constexpr int kLanes = 4;
+    P.lane.assign(NN, 0);
+    int nl_used = 1;
+    if (kind == K_PR || kind == K_MAR) {
+        std::vector<double> work(NN, 0.0);
+        for (int id = n; id < NN; ++id) {
             const Node &nd = pl.node[id];
-            for (int c : {nd.a, nd.b})
-                if (P.need_adj[c]) P.adj[c].off = A.alloc(P.adj[c].elems);
-            if (!P.micro[id]) A.release(P.adj[id].off, P.adj[id].elems);
+            work[id] = (P.micro[id] ? 0.0 : (double)P.fwd[id].elems) + work[nd.a] + work[nd.b];
+        }
+        const double total = work[pl.root];
+        int next = 0;
+        for (int id = NN - 1; id >= n; --id) {
+            const Node &nd = pl.node[id];
+            int heavy = work[nd.a] >= work[nd.b] ? nd.a : nd.b;
+            int light = heavy == nd.a ? nd.b : nd.a;
+            P.lane[heavy] = P.lane[id];
+            P.lane[light] = P.lane[id];
+            if (light >= n && !P.micro[light] && work[light] >= 0.03 * total) {
+                P.lane[light] = (P.lane[id] + 1 + (next++ % (kLanes - 1))) % kLanes;
+                nl_used = kLanes;
+            }
         }
     }
-    P.arena_elems = A.top;
+    auto plan_arena = [&](bool recycle) {
+        OffsetAlloc A;
+        for (int id = 0; id < n; ++id) P.fwd[id].off = A.alloc(P.fwd[id].elems);
+        // Micro subtrees run concurrently (one CTA each), so memory is never
+        // recycled inside the micro phase; their tensors are tiny.
+        for (int id : fwd_order) {
+            const Node &nd = pl.node[id];
+            P.fwd[id].off = A.alloc(P.fwd[id].elems);
+            if (recycle && !keep_all && !P.micro[id]) {
+                A.release(P.fwd[nd.a].off, P.fwd[nd.a].elems);
+                A.release(P.fwd[nd.b].off, P.fwd[nd.b].elems);
+            }
+        }
+        if (backward) {
+            P.adj[pl.root].off = A.alloc(P.adj[pl.root].elems);
+            for (int id : bwd_order) {
+                const Node &nd = pl.node[id];
+                for (int c : {nd.a, nd.b})
+                    if (P.need_adj[c]) P.adj[c].off = A.alloc(P.adj[c].elems);
+                if (recycle && !P.micro[id]) A.release(P.adj[id].off, P.adj[id].elems);
+            }
+        }
+        return A.top;
+    };
+    if (nl_used > 1) {
+        // lanes only where the unrecycled arena stays modest
+        int64_t rec = plan_arena(true), all = plan_arena(false);
+        if ((double)all * P.esz > std::max(4.0e9, 1.5 * (double)rec * P.esz)) {
+            nl_used = 1;
+            std::fill(P.lane.begin(), P.lane.end(), 0);
+        }
+    }
+    P.nlanes = nl_used;
+    int64_t arena_top = plan_arena(nl_used == 1);
+    P.arena_elems = arena_top;
     // argmax buffers
     int64_t am_total = 0;
     P.am_off.assign(NN, -1);
@@ -1203,6 +1259,7 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
             err = add_gemm(P.fsteps, X, Y, nd.gbt, nd.gm, nd.gn, nd.elim, nd.labels, nd.beta,
                            fptr(id), P.mx + P.fwd[id].mx, flops, bytes);
             if (!err.empty()) return fail(TN_E_UNSUPPORTED, err);
+            P.fsteps.back().node = id;
         } else {
             Step st;
             st.semiring = maxplus ? MAXPLUS : SUM;
@@ -1235,6 +1292,7 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                 st.d = d;
                 scratch = std::max(scratch, contract_scratch_bytes(d, P.esz));
             }
+            st.node = id;
             P.fsteps.push_back(st);
         }
     }
@@ -1259,6 +1317,8 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                                    P.adj_beta[nd.ga], aptr(nd.ga), P.mx + P.adj[nd.ga].mx, flops,
                                    bytes);
                     if (!err.empty()) return fail(TN_E_UNSUPPORTED, err);
+                    P.bsteps.back().node = nd.ga;
+                    P.bsteps.back().adjoint = true;
                 }
                 if (P.need_adj[nd.gb]) {
                     // Bbar[bt, k, n] = sum_m A[bt, m, k] Cbar[bt, m, n]
@@ -1268,6 +1328,8 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                                    P.adj_beta[nd.gb], aptr(nd.gb), P.mx + P.adj[nd.gb].mx, flops,
                                    bytes);
                     if (!err.empty()) return fail(TN_E_UNSUPPORTED, err);
+                    P.bsteps.back().node = nd.gb;
+                    P.bsteps.back().adjoint = true;
                 }
                 continue;
             }
@@ -1298,6 +1360,8 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                     st.why = absorb_reject;
                     scratch = std::max(scratch, contract_scratch_bytes(st.d, P.esz));
                 }
+                st.node = nd.a;
+                st.adjoint = true;
                 P.bsteps.push_back(st);
             }
             if (P.need_adj[nd.b]) {
@@ -1335,6 +1399,8 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                     st.why = absorb_reject;
                     scratch = std::max(scratch, contract_scratch_bytes(st.d, P.esz));
                 }
+                st.node = nd.b;
+                st.adjoint = true;
                 P.bsteps.push_back(st);
             }
         }
@@ -1391,6 +1457,40 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
         CK(P.mem.alloc(&P.d_mb_beg, 4 * P.mb_beg.size()));
         CK(cudaMemcpy(P.d_mb_beg, P.mb_beg.data(), 4 * P.mb_beg.size(), cudaMemcpyHostToDevice));
     }
+    // ---- step lanes and the events that order them across lanes: event id
+    // for fwd[v] = v, for adj[v] = NN + v (the root adjoint's is recorded
+    // after it is set to one), 2 NN = start, 2 NN + 1 + l = end of lane l
+    {
+        std::vector<int> prod_f(NN, -1), prod_b(NN, -1);
+        for (int i = 0; i < (int)P.fsteps.size(); ++i) {
+            Step &st = P.fsteps[i];
+            st.lane = st.node >= 0 ? P.lane[st.node] : 0;
+            if (st.node >= 0) prod_f[st.node] = i;
+        }
+        for (int i = 0; i < (int)P.bsteps.size(); ++i) {
+            Step &st = P.bsteps[i];
+            st.lane = st.node >= 0 ? P.lane[st.node] : 0;
+            if (st.node >= 0) prod_b[st.node] = i;
+        }
+        if (P.nlanes > 1) {
+            for (auto &st : P.fsteps) {
+                if (st.node < 0) continue;
+                const Node &nd = pl.node[st.node];
+                for (int c : {nd.a, nd.b})
+                    if (c >= n && !P.micro[c] && P.lane[c] != st.lane && prod_f[c] >= 0) {
+                        st.waits.push_back(c);
+                        P.fsteps[prod_f[c]].rec = c;
+                    }
+            }
+            for (auto &st : P.bsteps) {
+                if (st.node < 0) continue;
+                const int par = pl.node[st.node].parent;
+                if (par < 0 || P.lane[par] == st.lane) continue;
+                st.waits.push_back(NN + par);
+                if (par != pl.root && prod_b[par] >= 0) P.bsteps[prod_b[par]].rec = NN + par;
+            }
+        }
+    }
     trace_program(P);
     // inner offset tables of the streaming steps, one device buffer
     {
@@ -1426,36 +1526,55 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
             for (auto &w : pwhere) w.first->tl.ttab = dt + w.second;
         }
     }
-    // GEMM workspaces, then patch the steps' workspace pointers
-    if (need_x) CK(P.mem.alloc(&P.wsX, need_x));
-    if (need_y) CK(P.mem.alloc(&P.wsY, need_y));
-    if (need_d) CK(P.mem.alloc(&P.wsD, need_d));
-    for (auto *steps : {&P.fsteps, &P.bsteps})
-        for (auto &st : *steps) {
-            if (st.kind != 1) continue;
-            st.g.px.out = P.wsX;
-            st.g.py.out = P.wsY;
-            st.g.g.X = P.wsX;
-            st.g.g.Y = P.wsY;
-            if (st.g.has_post) {
-                st.g.g.D = P.wsD;
-                st.g.post.in = P.wsD;
-            }
-            st.g.tc = st.g.tc && tc_gemm_supported(st.g.g);
+    // GEMM workspaces (one set per lane that runs GEMM steps), then patch
+    // the steps' workspace pointers
+    {
+        std::vector<char> has_gemm(P.nlanes, 0);
+        for (auto *steps : {&P.fsteps, &P.bsteps})
+            for (auto &st : *steps)
+                if (st.kind == 1) has_gemm[st.lane] = 1;
+        std::vector<std::array<char *, 3>> ws(P.nlanes, {nullptr, nullptr, nullptr});
+        for (int l = 0; l < P.nlanes; ++l) {
+            if (!has_gemm[l]) continue;
+            if (need_x) CK(P.mem.alloc(&ws[l][0], need_x));
+            if (need_y) CK(P.mem.alloc(&ws[l][1], need_y));
+            if (need_d) CK(P.mem.alloc(&ws[l][2], need_d));
         }
+        P.wsX = ws[0][0];
+        P.wsY = ws[0][1];
+        P.wsD = ws[0][2];
+        for (auto *steps : {&P.fsteps, &P.bsteps})
+            for (auto &st : *steps) {
+                if (st.kind != 1) continue;
+                char *wx = ws[st.lane][0], *wy = ws[st.lane][1], *wd = ws[st.lane][2];
+                st.g.px.out = wx;
+                st.g.py.out = wy;
+                st.g.g.X = wx;
+                st.g.g.Y = wy;
+                if (st.g.has_post) {
+                    st.g.g.D = wd;
+                    st.g.post.in = wd;
+                }
+                st.g.tc = st.g.tc && tc_gemm_supported(st.g.g);
+            }
+    }
     P.scratch_bytes = scratch;
-    if (scratch) CK(P.mem.alloc(&P.scratch, scratch));
+    P.lscratch.assign(P.nlanes, nullptr);
+    if (scratch)
+        for (int l = 0; l < P.nlanes; ++l) CK(P.mem.alloc(&P.lscratch[l], scratch));
+    P.scratch = P.lscratch[0];
     // completion counters of the reduce steps (one per group and item)
     P.nrcnt = 0;
     for (auto *steps : {&P.fsteps, &P.bsteps})
         for (auto &st : *steps)
             if (st.kind == 3) P.nrcnt = std::max<int64_t>(P.nrcnt, st.rd.ng * st.rd.nbeta);
     if (P.nrcnt) {
-        CK(P.mem.alloc(&P.rcnt, (size_t)P.nrcnt * 4));
-        CK(cudaMemset(P.rcnt, 0, (size_t)P.nrcnt * 4));
+        // one counter set per lane, contiguous so that one memset clears all
+        CK(P.mem.alloc(&P.rcnt, (size_t)P.nrcnt * P.nlanes * 4));
+        CK(cudaMemset(P.rcnt, 0, (size_t)P.nrcnt * P.nlanes * 4));
         for (auto *steps : {&P.fsteps, &P.bsteps})
             for (auto &st : *steps)
-                if (st.kind == 3) st.rd.cnt = P.rcnt;
+                if (st.kind == 3) st.rd.cnt = P.rcnt + (size_t)st.lane * P.nrcnt;
     }
     // ---- leaf records to device
     CK(P.mem.alloc(&P.d_leaf, sizeof(LeafRec) * n));
@@ -1642,14 +1761,15 @@ static void run_step(tn_model *m, Program &P, const Step &s, cudaStream_t st, in
         return;
     }
     if (s.kind == 3) {
-        timed(pr, st, C_SPLITK, s.flops, s.bytes, [&] { launch_reduce<T>(s.rd, P.scratch, st); });
+        timed(pr, st, C_SPLITK, s.flops, s.bytes,
+              [&] { launch_reduce<T>(s.rd, P.lscratch[s.lane], st); });
         nl += reduce_launches(s.rd);
         return;
     }
     if (s.kind == 0) {
         int cls = contract_uses_splitk(s.d) ? C_SPLITK : C_GENERIC;
         timed(pr, st, cls, s.flops, s.bytes, [&] {
-            launch_contract<T>(s.d, s.semiring, P.scratch, P.scratch_bytes, st, &nl);
+            launch_contract<T>(s.d, s.semiring, P.lscratch[s.lane], P.scratch_bytes, st, &nl);
         });
         return;
     }
@@ -1671,14 +1791,17 @@ static void run_step(tn_model *m, Program &P, const Step &s, cudaStream_t st, in
     }
 }
 
+// `lanes` (capture only): the streams of lanes 1 .. nlanes-1; without them
+// every step runs in order on `st`.
 template <typename T>
-void enqueue_program(tn_model *m, Program &P, cudaStream_t st, Prof *pr = nullptr) {
+void enqueue_program(tn_model *m, Program &P, cudaStream_t st, Prof *pr = nullptr,
+                     const std::vector<cudaStream_t> *lanes = nullptr) {
     const Plan &pl = P.plan;
     const int n = pl.tree.nleaves, NN = 2 * n - 1;
     const bool maxplus = P.kind == K_MAP || P.kind == K_MAXNET;
     int nl = 0;
     cudaMemsetAsync(P.mx, 0, (size_t)P.nmx * 8, st);
-    if (P.nrcnt) cudaMemsetAsync(P.rcnt, 0, (size_t)P.nrcnt * 4, st);
+    if (P.nrcnt) cudaMemsetAsync(P.rcnt, 0, (size_t)P.nrcnt * P.nlanes * 4, st);
     ++nl;
     launch_leaves<T>(P.d_leaf, P.nleafrec, m->d_tables, P.d_card, m->md.nvars, P.d_evid, P.nbeta,
                      maxplus ? 1 : 0, (T *)P.arena, P.mx, m->d_flags, P.d_slice_val, st);
@@ -1690,7 +1813,29 @@ void enqueue_program(tn_model *m, Program &P, cudaStream_t st, Prof *pr = nullpt
         });
         ++nl;
     }
-    for (auto &s : P.fsteps) run_step<T>(m, P, s, st, nl, pr);
+    const bool par = lanes && P.nlanes > 1 && (int)P.ev.size() >= 2 * NN + 1 + P.nlanes;
+    auto lane_stream = [&](int l) { return (par && l > 0) ? (*lanes)[l - 1] : st; };
+    auto run_steps = [&](std::vector<Step> &steps) {
+        for (auto &s : steps) {
+            cudaStream_t ls = lane_stream(s.lane);
+            if (par)
+                for (int w : s.waits) cudaStreamWaitEvent(ls, P.ev[w], 0);
+            run_step<T>(m, P, s, ls, nl, pr);
+            if (par && s.rec >= 0) cudaEventRecord(P.ev[s.rec], ls);
+        }
+    };
+    auto join_lanes = [&] {
+        for (int l = 1; par && l < P.nlanes; ++l) {
+            cudaEventRecord(P.ev[2 * NN + 1 + l], lane_stream(l));
+            cudaStreamWaitEvent(st, P.ev[2 * NN + 1 + l], 0);
+        }
+    };
+    if (par) {
+        cudaEventRecord(P.ev[2 * NN], st);
+        for (int l = 1; l < P.nlanes; ++l) cudaStreamWaitEvent(lane_stream(l), P.ev[2 * NN], 0);
+    }
+    run_steps(P.fsteps);
+    if (P.kind != K_MAR) join_lanes();
     const Slot &rs = P.fwd[pl.root];
     if (P.kind != K_SUMNET && P.kind != K_MAXNET) {
         launch_logz<T>(P.nbeta, (const T *)P.arena + rs.off, rs.beta ? 1 : 0, P.mx, P.d_exps,
@@ -1705,7 +1850,9 @@ void enqueue_program(tn_model *m, Program &P, cudaStream_t st, Prof *pr = nullpt
         const Slot &ra = P.adj[pl.root];
         launch_fill_one<T>((T *)P.arena + ra.off, ra.elems, P.mx + ra.mx, st);
         ++nl;
-        for (auto &s : P.bsteps) run_step<T>(m, P, s, st, nl, pr);
+        if (par) cudaEventRecord(P.ev[NN + pl.root], st);
+        run_steps(P.bsteps);
+        join_lanes();
         if (!P.mb.empty()) {
             timed(pr, st, C_SMALL, 0, 0, [&] {
                 launch_micro<T>(P.d_mb, P.d_mb_beg, (int)P.mb_beg.size() - 1, SUM, (T *)P.arena,
@@ -1734,9 +1881,22 @@ void enqueue_program(tn_model *m, Program &P, cudaStream_t st, Prof *pr = nullpt
 
 tn_status capture_program(tn_model *m, Program &P) {
     cudaGraph_t g = nullptr;
+    if (P.nlanes > 1) {
+        while ((int)m->lanes.size() < P.nlanes - 1) {
+            cudaStream_t l;
+            CK(cudaStreamCreateWithFlags(&l, cudaStreamNonBlocking));
+            m->lanes.push_back(l);
+        }
+        const int NN = 2 * P.plan.tree.nleaves - 1;
+        while ((int)P.ev.size() < 2 * NN + 1 + P.nlanes) {
+            cudaEvent_t e;
+            CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            P.ev.push_back(e);
+        }
+    }
     CK(cudaStreamBeginCapture(m->stream, cudaStreamCaptureModeThreadLocal));
-    if (P.dtype == 0) enqueue_program<double>(m, P, m->stream);
-    else enqueue_program<float>(m, P, m->stream);
+    if (P.dtype == 0) enqueue_program<double>(m, P, m->stream, nullptr, &m->lanes);
+    else enqueue_program<float>(m, P, m->stream, nullptr, &m->lanes);
     cudaError_t e = cudaStreamEndCapture(m->stream, &g);
     if (e != cudaSuccess) return fail(TN_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     e = cudaGraphInstantiate(&P.gexec, g, 0);
@@ -1754,6 +1914,8 @@ tn_status ensure_device(tn_model *m) {
         if (m->d_tables) cudaFree(m->d_tables);
         m->d_tables = nullptr;
         if (m->stream) cudaStreamDestroy(m->stream);
+        for (auto l : m->lanes) cudaStreamDestroy(l);
+        m->lanes.clear();
         if (m->ev0) cudaEventDestroy(m->ev0);
         if (m->ev1) cudaEventDestroy(m->ev1);
         CK(cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking));
