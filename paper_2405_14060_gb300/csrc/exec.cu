@@ -195,6 +195,7 @@ struct Program {
     std::vector<void *> lscratch;              // per lane: reduce / split-K scratch
     std::vector<unsigned int *> lrcnt;         // per lane: reduce completion counters
     std::vector<cudaEvent_t> ev;               // 2 NN + 2 + nlanes events (capture only)
+    std::vector<int> mlane_beg;                // micro subtrees of lane l: [beg[l], beg[l+1])
     ~Program() {
         if (gexec) cudaGraphExecDestroy(gexec);
         for (auto e : ev) cudaEventDestroy(e);
@@ -962,7 +963,8 @@ static void trace_program(const Program &P) {
             else
                 fprintf(stderr, "%s %d contract outs %lld k %lld [%s]", dir, i,
                         (long long)st.d.nout_total, (long long)st.d.ktotal, st.why);
-            fprintf(stderr, " MB %.3f MFLOP %.3f\n", st.bytes / 1e6, st.flops / 1e6);
+            fprintf(stderr, " MB %.3f MFLOP %.3f lane %d waits %d\n", st.bytes / 1e6, st.flops / 1e6,
+                    st.lane, (int)st.waits.size());
             ++i;
         }
     }
@@ -1405,8 +1407,19 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
             }
         }
     }
-    // micro lists
-    for (auto &kv : msub) {
+    // micro lists, grouped by the lane of their subtree (each lane runs its
+    // own subtrees first in the forward pass and last in the backward pass)
+    std::vector<std::pair<int, int>> morder;   // (lane, micro root)
+    for (auto &kv : msub) morder.push_back({P.lane[kv.first], kv.first});
+    std::stable_sort(morder.begin(), morder.end(),
+                     [](const std::pair<int, int> &x, const std::pair<int, int> &y) {
+                         return x.first < y.first;
+                     });
+    P.mlane_beg.assign(P.nlanes + 1, 0);
+    for (auto &lo : morder) P.mlane_beg[lo.first + 1]++;
+    for (int l = 0; l < P.nlanes; ++l) P.mlane_beg[l + 1] += P.mlane_beg[l];
+    for (auto &lo : morder) {
+        auto &kv = *msub.find(lo.second);
         P.mf_beg.push_back((int32_t)P.mf.size());
         for (int id : kv.second) {
             MicroDesc md;
@@ -1806,15 +1819,31 @@ void enqueue_program(tn_model *m, Program &P, cudaStream_t st, Prof *pr = nullpt
     launch_leaves<T>(P.d_leaf, P.nleafrec, m->d_tables, P.d_card, m->md.nvars, P.d_evid, P.nbeta,
                      maxplus ? 1 : 0, (T *)P.arena, P.mx, m->d_flags, P.d_slice_val, st);
     ++nl;
-    if (!P.mf.empty()) {
-        timed(pr, st, C_SMALL, 0, 0, [&] {
-            launch_micro<T>(P.d_mf, P.d_mf_beg, (int)P.mf_beg.size() - 1, maxplus ? MAXPLUS : SUM,
-                            (T *)P.arena, P.mx, P.am, st);
-        });
-        ++nl;
-    }
     const bool par = lanes && P.nlanes > 1 && (int)P.ev.size() >= 2 * NN + 1 + P.nlanes;
     auto lane_stream = [&](int l) { return (par && l > 0) ? (*lanes)[l - 1] : st; };
+    if (par) {
+        cudaEventRecord(P.ev[2 * NN], st);
+        for (int l = 1; l < P.nlanes; ++l) cudaStreamWaitEvent(lane_stream(l), P.ev[2 * NN], 0);
+    }
+    // micro subtrees: one launch, or one per lane when the lanes run apart
+    auto micro = [&](const MicroDesc *d, const int32_t *beg, int sem) {
+        if (!par) {
+            int ns = (int)P.mlane_beg.back();
+            if (ns > 0) {
+                timed(pr, st, C_SMALL, 0, 0,
+                      [&] { launch_micro<T>(d, beg, ns, sem, (T *)P.arena, P.mx, P.am, st); });
+                ++nl;
+            }
+            return;
+        }
+        for (int l = 0; l < P.nlanes; ++l) {
+            int s0 = P.mlane_beg[l], s1 = P.mlane_beg[l + 1];
+            if (s1 <= s0) continue;
+            launch_micro<T>(d, beg + s0, s1 - s0, sem, (T *)P.arena, P.mx, P.am, lane_stream(l));
+            ++nl;
+        }
+    };
+    if (!P.mf.empty()) micro(P.d_mf, P.d_mf_beg, maxplus ? MAXPLUS : SUM);
     auto run_steps = [&](std::vector<Step> &steps) {
         for (auto &s : steps) {
             cudaStream_t ls = lane_stream(s.lane);
@@ -1830,10 +1859,6 @@ void enqueue_program(tn_model *m, Program &P, cudaStream_t st, Prof *pr = nullpt
             cudaStreamWaitEvent(st, P.ev[2 * NN + 1 + l], 0);
         }
     };
-    if (par) {
-        cudaEventRecord(P.ev[2 * NN], st);
-        for (int l = 1; l < P.nlanes; ++l) cudaStreamWaitEvent(lane_stream(l), P.ev[2 * NN], 0);
-    }
     run_steps(P.fsteps);
     if (P.kind != K_MAR) join_lanes();
     const Slot &rs = P.fwd[pl.root];
@@ -1852,14 +1877,8 @@ void enqueue_program(tn_model *m, Program &P, cudaStream_t st, Prof *pr = nullpt
         ++nl;
         if (par) cudaEventRecord(P.ev[NN + pl.root], st);
         run_steps(P.bsteps);
+        if (!P.mb.empty()) micro(P.d_mb, P.d_mb_beg, SUM);
         join_lanes();
-        if (!P.mb.empty()) {
-            timed(pr, st, C_SMALL, 0, 0, [&] {
-                launch_micro<T>(P.d_mb, P.d_mb_beg, (int)P.mb_beg.size() - 1, SUM, (T *)P.arena,
-                                P.mx, P.am, st);
-            });
-            ++nl;
-        }
         launch_marginals<T>(P.d_margrec, m->md.nvars, P.nbeta, (const T *)P.arena,
                             (const T *)P.arena, P.d_marg, P.marg_stride, st);
         ++nl;
