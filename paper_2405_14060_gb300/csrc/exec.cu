@@ -122,6 +122,7 @@ struct GemmOp {
     std::vector<int32_t> tpx, tpy, tpost;   // tiled-permutation tables (host copies)
     bool has_post = false;
     bool direct = false;
+    bool x_in_place = false;   // X already in GEMM form: read in place, its scale in the epilogue
     bool tc = false;
     GDesc g;
     double prep_bytes = 0, post_bytes = 0;
@@ -544,6 +545,16 @@ static std::string make_gemm_op(const std::vector<int> &card, int nbeta, int sto
         op.has_post = true;
         op.post_bytes = (double)B * R * C * ssz * 2;
         nd = (size_t)(B * R * C) * ssz;
+    }
+    // X already laid out as [batch][rows][K] in the GEMM input type (an
+    // identity preparation), 16-byte aligned, one scale for all items: the
+    // GEMM reads it in place and applies the scale to D
+    if (op.px.nd == 1 && op.px.sin[0] == 1 && op.px.sout[0] == 1 && K == Kld &&
+        store_t == gemm_t && !X.beta && X.ptr && ((uintptr_t)X.ptr & 15) == 0) {
+        op.x_in_place = true;
+        op.g.X = X.ptr;
+        op.g.mxsx = X.mx;
+        op.prep_bytes -= (double)(B * R * K) * (ssz + gsz);
     }
     plan_permute_tiles(op.px, op.tpx);
     plan_permute_tiles(op.py, op.tpy);
@@ -1562,7 +1573,7 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                 char *wx = ws[st.lane][0], *wy = ws[st.lane][1], *wd = ws[st.lane][2];
                 st.g.px.out = wx;
                 st.g.py.out = wy;
-                st.g.g.X = wx;
+                if (!st.g.x_in_place) st.g.g.X = wx;
                 st.g.g.Y = wy;
                 if (st.g.has_post) {
                     st.g.g.D = wd;
@@ -1788,10 +1799,10 @@ static void run_step(tn_model *m, Program &P, const Step &s, cudaStream_t st, in
     }
     const GemmOp &g = s.g;
     timed(pr, st, C_PREP, 0, g.prep_bytes, [&] {
-        launch_permute(g.px, st);
+        if (!g.x_in_place) launch_permute(g.px, st);
         launch_permute(g.py, st);
     });
-    nl += 2;
+    nl += g.x_in_place ? 1 : 2;
     if (g.tc) {
         timed(pr, st, C_TCGEMM, s.flops, s.bytes, [&] { launch_tc_gemm(g.g, m->d_err, st); });
     } else {

@@ -306,6 +306,7 @@ constexpr unsigned long long TC_WAIT_NS = 2000000000ull;
 struct TCParams {
     int64_t R, C, ldd, bsd;
     int64_t ntn, ntm;           // column / row tiles (grid.x = batch x rows x columns)
+    const unsigned long long *mxsx;   // scale of X applied to D (NULL: none)
     int kt;                     // number of 128-byte K slabs
     float *D;
     unsigned long long *mxd;
@@ -469,9 +470,11 @@ __global__ void __launch_bounds__(128, 1)
     tc_fence_after();
     const int64_t row = m0 + warp * 32 + lane;
     float mx = 0;
+    const float sxs = p.mxsx ? pow2neg<float>(exp_of_bits(*p.mxsx)) : 1.f;
     if (have) {
         float *drow = p.D + (int64_t)bz * p.bsd + row * p.ldd;
         for (int ch = 0; ch < TC_BN / 32; ++ch) {
+            if (n0 + ch * 32 >= p.C) break;   // warp-uniform: no columns left
             uint32_t r[32];
             uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 32);
             asm volatile(
@@ -493,16 +496,16 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         float4 v;
-                        v.x = __uint_as_float(r[4 * q + 0]);
-                        v.y = __uint_as_float(r[4 * q + 1]);
-                        v.z = __uint_as_float(r[4 * q + 2]);
-                        v.w = __uint_as_float(r[4 * q + 3]);
+                        v.x = __uint_as_float(r[4 * q + 0]) * sxs;
+                        v.y = __uint_as_float(r[4 * q + 1]) * sxs;
+                        v.z = __uint_as_float(r[4 * q + 2]) * sxs;
+                        v.w = __uint_as_float(r[4 * q + 3]) * sxs;
                         dst[q] = v;
                         mx = fmaxf(mx, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
                     }
                 } else {
                     for (int q = 0; q < 32 && c0 + q < p.C; ++q) {
-                        float v = __uint_as_float(r[q]);
+                        float v = __uint_as_float(r[q]) * sxs;
                         drow[c0 + q] = v;
                         mx = fmaxf(mx, v);
                     }
@@ -581,6 +584,7 @@ cudaError_t launch_tc_gemm(const GDesc &g, int *err_flag, cudaStream_t st) {
     p.kt = (int)((g.K + kel - 1) / kel);
     p.D = (float *)g.D;
     p.mxd = g.mxd;
+    p.mxsx = g.mxsx;
     p.beta_div_batch = g.beta_div_batch;
     p.beta_div_row = g.beta_div_row;
     p.err = err_flag;
@@ -637,6 +641,7 @@ __global__ void __launch_bounds__(256) k_simt_gemm(const __grid_constant__ GDesc
     }
     T mx = 0;
     T *D = (T *)g.D + b * g.bsd;
+    const T sxs = g.mxsx ? pow2neg<T>(exp_of_bits(*g.mxsx)) : T(1);
     int64_t rowlast = r0 + ty * 4;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -647,8 +652,9 @@ __global__ void __launch_bounds__(256) k_simt_gemm(const __grid_constant__ GDesc
         for (int j = 0; j < 4; ++j) {
             int64_t c = c0 + tx * 4 + j;
             if (c < g.C) {
-                D[r * g.ldd + c] = acc[i][j];
-                mx = mx > acc[i][j] ? mx : acc[i][j];
+                const T v = acc[i][j] * sxs;
+                D[r * g.ldd + c] = v;
+                mx = mx > v ? mx : v;
             }
         }
     }

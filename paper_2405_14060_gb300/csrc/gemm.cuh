@@ -65,6 +65,7 @@ struct GDesc {
     const void *X, *Y;
     void *D;
     unsigned long long *mxd;        // per-item max of D (NULL: none)
+    const unsigned long long *mxsx; // X read in place: D is scaled by 2^-e of this maximum
     int64_t beta_div_batch;         // item = b / beta_div_batch (if > 0)
     int64_t beta_div_row;           // else item = r / beta_div_row (if > 0), else 0
 };
