@@ -44,6 +44,24 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// Quotient and remainder of a non-negative tile index by a positive count:
+// a shift when the count is a power of two (lb = its log2, else -1), 32-bit
+// division when both fit, 64-bit division otherwise.
+__device__ __forceinline__ int64_t div_tile(int64_t a, int64_t b, int lb, int64_t &rem) {
+    int64_t q;
+    if (lb >= 0) q = a >> lb;
+    else if (((uint64_t)a | (uint64_t)b) < (1ull << 32)) q = (int64_t)((uint32_t)a / (uint32_t)b);
+    else q = a / b;
+    rem = a - q * b;
+    return q;
+}
+__host__ __device__ __forceinline__ int log2_if_pow2(int64_t b) {
+    if (b <= 0 || (b & (b - 1))) return -1;
+    int l = 0;
+    while ((1ll << l) < b) ++l;
+    return l;
+}
+
 __device__ __forceinline__ unsigned long long dbits(double x) {
     return (unsigned long long)__double_as_longlong(x);
 }

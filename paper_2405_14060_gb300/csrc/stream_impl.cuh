@@ -50,9 +50,11 @@ __global__ void __launch_bounds__(256) k_absorb(const __grid_constant__ ADesc d)
     // tiles: (outer index, chunk of 256 U inner positions)
     const int nch = (nin + 256 * U - 1) / (256 * U);
     const int64_t ntile = d.nouter * nch;
+    const int lnch = log2_if_pow2(nch);
     for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-        const int64_t o = tile / nch;
-        const int c = (int)(tile - o * nch);
+        int64_t crem;
+        const int64_t o = div_tile(tile, nch, lnch, crem);
+        const int c = (int)crem;
         int64_t bx = beta * d.bsx, by = beta * d.bsy, bw = beta * d.bsw;
         if (d.pow2r) {
             const int64_t r0 = o * nin;
@@ -180,9 +182,11 @@ __global__ void __launch_bounds__(256) k_absorb_sm(const __grid_constant__ ADesc
     T mx = 0;
     const int nch = (nin + 256 * U - 1) / (256 * U);
     const int64_t ntile = d.nouter * nch;
+    const int lnch = log2_if_pow2(nch);
     for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-        const int64_t o = tile / nch;
-        const int c = (int)(tile - o * nch);
+        int64_t crem;
+        const int64_t o = div_tile(tile, nch, lnch, crem);
+        const int c = (int)crem;
         int64_t bx = beta * d.bsx, by = beta * d.bsy;
         int cb = 0;
         if (d.pow2r) {
@@ -385,11 +389,13 @@ __global__ void __launch_bounds__(256) k_reduce_part(const __grid_constant__ RDe
     const int nk = t1 > t0 ? (int)(t1 - t0) : 0;
     const T *X = (const T *)d.X, *Z = (const T *)d.Z;
     const int s0 = bs * NS, z0 = bt * NT;
+    const int lcper = log2_if_pow2(cper);
     auto issue = [&](int k) {
         T *sb = buf + (k % S) * W * 256;
         const int64_t tile = t0 + k;
-        const int64_t o = tile / cper;
-        const int j = (int)(tile - o * cper) * pp + p;
+        int64_t crem;
+        const int64_t o = div_tile(tile, cper, lcper, crem);
+        const int j = (int)crem * pp + p;
         if (j < nin) {
             int64_t bx = gx, bz = gz;
             if (d.pow2m) {
