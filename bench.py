@@ -225,6 +225,35 @@ def _fp64_torch_baseline(model, l, r):
     return (time.perf_counter() - t0) / reps, float(lz.detach())
 
 
+def _task_extras():
+    """Throughput of the tropical tasks on their workload (a second or two):
+    MAP and MMAP on the 300-variable banded Bayesian network with 20% of the
+    variables observed.  Device time from the library's CUDA events, wall
+    time through the host-pointer C ABI.  The batched and sliced workloads
+    take minutes and are timed by their parity tests instead."""
+    from paper_2405_14060_gb300 import synth, tn
+    out = {}
+    w3 = synth.workload(3)
+    M = tn.Model.from_synth(w3.model)
+
+    def timed(fn, reps):
+        fn()
+        t0 = time.perf_counter()
+        dev = 0.0
+        for _ in range(reps):
+            fn()
+            dev += M.last_device_ms()
+        return (time.perf_counter() - t0) / reps, dev / reps
+
+    wall, dev = timed(lambda: M.map(w3.evid, prec="fp32"), 20)
+    out["map_bn300_fp32"] = {"solves_per_s": 1.0 / wall, "device_ms": dev,
+                             "config": "300 vars, 60 observed, greedy tree, max-plus FP32"}
+    wall, dev = timed(lambda: M.mmap(w3.query, w3.evid, prec="fp32"), 10)
+    out["mmap_bn300_fp32"] = {"solves_per_s": 1.0 / wall, "device_ms": dev,
+                              "config": f"{len(w3.query)} query vars, sum phase then max-plus"}
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_2405_14060_gb300 import tn
@@ -358,6 +387,13 @@ def run_ours(args):
                          f"the row-sweep order ({dt:.1f} s), scaled by the symbolic work ratio "
                          f"{wf / wp:.2f} to a full PR and x3 to PR+MAR"}
 
+    tasks = None
+    if not args.skip_tasks:
+        try:
+            tasks = _task_extras()
+        except Exception as e:  # reported, never fails the bench line
+            tasks = {"error": str(e)[:200]}
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -370,7 +406,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
         "gpu_launches": int(launches * args.steps), "clocks": clk.summary(),
-        "accuracy": acc, "fp64_baseline": fp64, "profile": prof_out,
+        "accuracy": acc, "fp64_baseline": fp64, "profile": prof_out, "tasks": tasks,
     }
     print(json.dumps(line), flush=True)
     if dist:
@@ -386,6 +422,8 @@ def main():
     ap.add_argument("--prec", default="tf32", choices=["fp64", "fp32", "tf32", "bf16"])
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-torch-fp64", action="store_true")
+    ap.add_argument("--skip-tasks", action="store_true",
+                    help="skip the MAP / MMAP throughput extras")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
