@@ -1711,11 +1711,11 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
             meta.push_back(P.fwd[nd.a].off);
             meta.push_back(P.fwd[nd.b].off);
             meta.push_back(K);
-            if (K > 4096) {
-                int64_t rows = P.fwd[id].per;
-                if ((double)rows * (double)K > (double)(1LL << 27))
-                    return fail(TN_E_UNSUPPORTED,
-                                "sampling: a node sums too many labels for its output size");
+            // large summed spaces get cumulative tables (binary search per
+            // sample) while those fit 2^27 entries; otherwise every sample
+            // scans the node's summed space directly
+            const int64_t rows = P.fwd[id].per;
+            if (K > 4096 && (double)rows * (double)K <= (double)(1LL << 27)) {
                 meta.push_back(cdf_total);
                 P.cdf_nodes.push_back({P.fdesc[id - n], rows});
                 cdf_total += rows * K;

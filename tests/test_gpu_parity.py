@@ -336,6 +336,21 @@ def test_workload2_full_size():
         assert abs(M.pr(prec=prec)[0] - lz_ref) <= 1e-4 * abs(lz_ref), prec
 
 
+def test_sampling_grid24_large_nodes():
+    """Sampling on the 24 x 24 grid's benchmark tree, whose dense nodes sum
+    4096 labels over 2^24-entry outputs (scanned per sample rather than
+    tabulated): per-spin frequencies within 5 sigma of the FP64 marginals."""
+    w = synth.workload(2)
+    m = w.model
+    M = tn.Model.from_synth(m)
+    M.set_order(*M.reassociate(*M.optimize_order(0)))
+    _, marg = M.mar(prec="fp64")
+    p1 = np.array([x[1] for x in M.split(marg[0])])
+    n = 20000
+    s = M.sample(n, seed=3, prec="tf32")
+    assert np.all(np.abs(s.mean(axis=0) - p1) < 5 * np.sqrt(p1 * (1 - p1) / n) + 2e-3)
+
+
 def test_reassociated_tree_batched_evidence():
     """A re-associated tree (absorption runs contracted small-first) on a
     14 x 14 grid with a batch of evidence sets: the combined small tensors
