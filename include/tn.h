@@ -205,6 +205,9 @@ tn_status tn_map(tn_model *m, const int32_t *evid, const tn_options *opts,
  * method of Sec. MMAP (sum-contract groups, then max-plus over the query).
  * The summed phase runs in FP64 when prec = TN_FP64, else in FP32 with
  * power-of-two rescaling; the max-plus phase runs in FP64 / FP32 likewise.
+ * The model keeps the programs of its last call: a call with the same query
+ * set, the same observed variables and the same precision only replays them
+ * with the new evidence values.
  * Errors: TN_E_ARG (query overlaps evidence, p(e) = 0), TN_E_OOM. */
 tn_status tn_mmap(tn_model *m, const int32_t *evid, int nq, const int32_t *query,
                   const tn_options *opts, int32_t *assign, double *logp);

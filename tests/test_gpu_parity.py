@@ -143,6 +143,15 @@ def test_mmap_small_and_workload3():
             x, lp = M.mmap(q, ev, prec=prec)
             np.testing.assert_array_equal(x, xb)
             assert abs(lp - lb) < (1e-9 if prec == "fp64" else 1e-3)
+        # same query and observed variables, other values: the cached
+        # programs replay with the new evidence
+        ev2 = ev.copy()
+        obs = np.nonzero(ev >= 0)[0]
+        ev2[obs] = (ev[obs] + 1) % m.card[obs]
+        xb2, lb2 = oracle.brute_mmap(m, q, ev2)
+        x2, lp2 = M.mmap(q, ev2, prec="fp32")
+        np.testing.assert_array_equal(x2, xb2)
+        assert abs(lp2 - lb2) < 1e-3
     w = synth.workload(3)
     xo, lo = oracle.ve_mmap(w.model, w.query, w.evid[0])
     M = tn.Model.from_synth(w.model)
