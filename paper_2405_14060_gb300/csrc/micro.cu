@@ -22,6 +22,7 @@ __global__ void __launch_bounds__(256) k_micro(const MicroDesc *__restrict__ nod
     for (int i = i0; i < i1; ++i) {
         const MicroDesc &d = nodes[i];
         const int nb = d.nbeta, nout = d.nout_total;
+        T tmax = 0;   // single item: this thread's maximum, reduced once per node
         if (SEMI == SUM)
             for (int b = threadIdx.x; b < nb; b += blockDim.x) smx[b] = 0ull;
         __syncthreads();
@@ -66,10 +67,14 @@ __global__ void __launch_bounds__(256) k_micro(const MicroDesc *__restrict__ nod
                             kb += dg * d.ksb[q];
                         }
                     }
-                    acc += (A[ka] * sa) * (B[kb] * sb);
+                    acc += A[ka] * B[kb];
                 }
+                acc *= sa * sb;   // exact: both are powers of two
                 arena[d.offC + idx] = acc;
-                if (d.mxc >= 0 && acc > T(0)) atomicMax(&smx[beta], dbits((double)acc));
+                if (d.mxc >= 0) {
+                    if (nb == 1) tmax = tmax > acc ? tmax : acc;
+                    else if (acc > T(0)) atomicMax(&smx[beta], dbits((double)acc));
+                }
             } else {
                 T best = -INFINITY;
                 int32_t bk = 0;
@@ -87,6 +92,15 @@ __global__ void __launch_bounds__(256) k_micro(const MicroDesc *__restrict__ nod
                 arena[d.offC + idx] = best;
                 if (d.amoff >= 0) am[d.amoff + idx] = bk;
             }
+        }
+        if (SEMI == SUM && d.mxc >= 0 && nb == 1) {
+            // one shared atomic per warp instead of one per output
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                T v = __shfl_xor_sync(0xffffffffu, tmax, o);
+                tmax = tmax > v ? tmax : v;
+            }
+            if ((threadIdx.x & 31) == 0 && tmax > T(0)) atomicMax(&smx[0], dbits((double)tmax));
         }
         __syncthreads();
         if (SEMI == SUM && d.mxc >= 0)
