@@ -254,6 +254,18 @@ def _task_extras():
     return out
 
 
+def aggregate_ranks(ms_local, steps, world, dist=None, device="cpu"):
+    """Whole-job throughput of `world` replicas: every rank solved `steps`
+    problems; the job's time is the slowest rank's (max over ranks)."""
+    ms = ms_local
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * steps / (ms / 1e3)
+
+
 def run_ours(args):
     import torch
     from paper_2405_14060_gb300 import tn
@@ -304,12 +316,7 @@ def run_ours(args):
         torch.cuda.profiler.stop()
     if dist:
         dist.barrier()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * args.steps / (ms / 1e3)
+    ms, value = aggregate_ranks(e0.elapsed_time(e1), args.steps, world, dist, "cuda")
 
     # end to end through the host-pointer C ABI: H2D evidence, D2H log Z + marginals
     ev_h = np.full((1, m.nvars), -1, np.int32)
