@@ -51,27 +51,38 @@ __global__ void __launch_bounds__(256) k_absorb(const __grid_constant__ ADesc d)
     const int nch = (nin + 256 * U - 1) / (256 * U);
     const int64_t ntile = d.nouter * nch;
     const int lnch = log2_if_pow2(nch);
-    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    // each block takes a contiguous range of tiles, so consecutive tiles
+    // mostly share their outer index and its decoded offsets
+    const int64_t tper = (ntile + gridDim.x - 1) / gridDim.x;
+    const int64_t tbeg = (int64_t)blockIdx.x * tper;
+    const int64_t tend = tbeg + tper < ntile ? tbeg + tper : ntile;
+    int64_t cur_o = -1, bx = 0, by = 0, bw = 0;
+    for (int64_t tile = tbeg; tile < tend; ++tile) {
         int64_t crem;
         const int64_t o = div_tile(tile, nch, lnch, crem);
         const int c = (int)crem;
-        int64_t bx = beta * d.bsx, by = beta * d.bsy, bw = beta * d.bsw;
-        if (d.pow2r) {
-            const int64_t r0 = o * nin;
-            for (int k = 0; k < nod; ++k) {
-                int64_t dg = (r0 >> d.rsh[k]) & (int64_t)(d.rsz[k] - 1);
-                bx += dg * d.rsx[k];
-                by += dg * d.rsy[k];
-                bw += dg * d.rsw[k];
-            }
-        } else {
-            int64_t r = o;
-            for (int k = nod - 1; k >= 0; --k) {
-                int64_t dg = r % d.rsz[k];
-                r /= d.rsz[k];
-                bx += dg * d.rsx[k];
-                by += dg * d.rsy[k];
-                bw += dg * d.rsw[k];
+        if (o != cur_o) {
+            cur_o = o;
+            bx = beta * d.bsx;
+            by = beta * d.bsy;
+            bw = beta * d.bsw;
+            if (d.pow2r) {
+                const int64_t r0 = o * nin;
+                for (int k = 0; k < nod; ++k) {
+                    int64_t dg = (r0 >> d.rsh[k]) & (int64_t)(d.rsz[k] - 1);
+                    bx += dg * d.rsx[k];
+                    by += dg * d.rsy[k];
+                    bw += dg * d.rsw[k];
+                }
+            } else {
+                int64_t r = o;
+                for (int k = nod - 1; k >= 0; --k) {
+                    int64_t dg = r % d.rsz[k];
+                    r /= d.rsz[k];
+                    bx += dg * d.rsx[k];
+                    by += dg * d.rsy[k];
+                    bw += dg * d.rsw[k];
+                }
             }
         }
         const T *Xb = (const T *)d.X + bx;
@@ -183,28 +194,39 @@ __global__ void __launch_bounds__(256) k_absorb_sm(const __grid_constant__ ADesc
     const int nch = (nin + 256 * U - 1) / (256 * U);
     const int64_t ntile = d.nouter * nch;
     const int lnch = log2_if_pow2(nch);
-    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    // contiguous tile range per block; the outer decode is reused while the
+    // outer index stays the same
+    const int64_t tper = (ntile + gridDim.x - 1) / gridDim.x;
+    const int64_t tbeg = (int64_t)blockIdx.x * tper;
+    const int64_t tend = tbeg + tper < ntile ? tbeg + tper : ntile;
+    int64_t cur_o = -1, bx = 0, by = 0;
+    int cb = 0;
+    for (int64_t tile = tbeg; tile < tend; ++tile) {
         int64_t crem;
         const int64_t o = div_tile(tile, nch, lnch, crem);
         const int c = (int)crem;
-        int64_t bx = beta * d.bsx, by = beta * d.bsy;
-        int cb = 0;
-        if (d.pow2r) {
-            const int64_t r0 = o * nin;
-            for (int k = 0; k < nod; ++k) {
-                int64_t dg = (r0 >> d.rsh[k]) & (int64_t)(d.rsz[k] - 1);
-                bx += dg * d.rsx[k];
-                by += dg * d.rsy[k];
-                cb += (int)dg * d.rshc[k];
-            }
-        } else {
-            int64_t r = o;
-            for (int k = nod - 1; k >= 0; --k) {
-                int64_t dg = r % d.rsz[k];
-                r /= d.rsz[k];
-                bx += dg * d.rsx[k];
-                by += dg * d.rsy[k];
-                cb += (int)dg * d.rshc[k];
+        if (o != cur_o) {
+            cur_o = o;
+            bx = beta * d.bsx;
+            by = beta * d.bsy;
+            cb = 0;
+            if (d.pow2r) {
+                const int64_t r0 = o * nin;
+                for (int k = 0; k < nod; ++k) {
+                    int64_t dg = (r0 >> d.rsh[k]) & (int64_t)(d.rsz[k] - 1);
+                    bx += dg * d.rsx[k];
+                    by += dg * d.rsy[k];
+                    cb += (int)dg * d.rshc[k];
+                }
+            } else {
+                int64_t r = o;
+                for (int k = nod - 1; k >= 0; --k) {
+                    int64_t dg = r % d.rsz[k];
+                    r /= d.rsz[k];
+                    bx += dg * d.rsx[k];
+                    by += dg * d.rsy[k];
+                    cb += (int)dg * d.rshc[k];
+                }
             }
         }
         const T *Xb = (const T *)d.X + bx;
@@ -390,32 +412,37 @@ __global__ void __launch_bounds__(256) k_reduce_part(const __grid_constant__ RDe
     const T *X = (const T *)d.X, *Z = (const T *)d.Z;
     const int s0 = bs * NS, z0 = bt * NT;
     const int lcper = log2_if_pow2(cper);
+    int64_t cur_o = -1, cbx = 0, cbz = 0;   // outer decode of the last tile
     auto issue = [&](int k) {
         T *sb = buf + (k % S) * W * 256;
         const int64_t tile = t0 + k;
         int64_t crem;
         const int64_t o = div_tile(tile, cper, lcper, crem);
         const int j = (int)crem * pp + p;
-        if (j < nin) {
-            int64_t bx = gx, bz = gz;
+        if (o != cur_o) {
+            cur_o = o;
+            cbx = gx;
+            cbz = gz;
             if (d.pow2m) {
                 const int64_t r0 = o * nin;
                 for (int q = 0; q < nod; ++q) {
                     int64_t dg = (r0 >> d.msh[q]) & (int64_t)(d.msz[q] - 1);
-                    bx += dg * d.msx[q];
-                    bz += dg * d.msz2[q];
+                    cbx += dg * d.msx[q];
+                    cbz += dg * d.msz2[q];
                 }
             } else {
                 int64_t r = o;
                 for (int q = nod - 1; q >= 0; --q) {
                     int64_t dg = r % d.msz[q];
                     r /= d.msz[q];
-                    bx += dg * d.msx[q];
-                    bz += dg * d.msz2[q];
+                    cbx += dg * d.msx[q];
+                    cbz += dg * d.msz2[q];
                 }
             }
-            const T *xp = X + bx + __ldg(tx + j);
-            const T *zp = Z + bz + __ldg(tz + j);
+        }
+        if (j < nin) {
+            const T *xp = X + cbx + __ldg(tx + j);
+            const T *zp = Z + cbz + __ldg(tz + j);
 #pragma unroll
             for (int s = 0; s < NS; ++s) {
                 if (s0 + s < d.ns) cp_async_el(sb + s * 256, xp + d.xoff[s0 + s]);
