@@ -13,6 +13,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <numeric>
 #include <random>
 #include <set>
@@ -629,7 +630,7 @@ static bool combo_offsets(const std::vector<int> &card, const Labels &labs, cons
 }
 
 // Why the last make_absorb call declined (plan trace only).
-static const char *absorb_reject = "";
+static thread_local const char *absorb_reject = "";
 
 // Absorb: X streamed once, W small; Y's labels = R (from X) + T (new).
 static bool make_absorb(const std::vector<int> &card, const Labels &lx, bool bx, int64_t perx,
@@ -3016,10 +3017,20 @@ tn_status tn_contract_dev(int nlabels, const int *sizes, int na, const int *labe
                 op.post.in = wd;
             }
             bool tc = (prec == TN_TF32 || prec == TN_BF16) && dtype == 1 && tc_gemm_supported(op.g);
-            static int *d_err = nullptr;
-            if (!d_err) {
-                CK(cudaMalloc(&d_err, 16));
-                CK(cudaMemset(d_err, 0, 16));
+            // one wait-timeout flag per device, created on first use
+            static std::mutex err_mu;
+            static std::map<int, int *> err_flags;
+            int *d_err = nullptr;
+            {
+                int dev = 0;
+                CK(cudaGetDevice(&dev));
+                std::lock_guard<std::mutex> lk(err_mu);
+                int *&f = err_flags[dev];
+                if (!f) {
+                    CK(cudaMalloc(&f, 16));
+                    CK(cudaMemset(f, 0, 16));
+                }
+                d_err = f;
             }
             launch_permute(op.px, st);
             launch_permute(op.py, st);
