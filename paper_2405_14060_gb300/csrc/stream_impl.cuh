@@ -51,15 +51,23 @@ __global__ void __launch_bounds__(256) k_absorb(const __grid_constant__ ADesc d)
     const int nch = (nin + 256 * U - 1) / (256 * U);
     const int64_t ntile = d.nouter * nch;
     const int lnch = log2_if_pow2(nch);
-    // each block takes a contiguous range of tiles, so consecutive tiles
-    // mostly share their outer index and its decoded offsets
-    const int64_t tper = (ntile + gridDim.x - 1) / gridDim.x;
-    const int64_t tbeg = (int64_t)blockIdx.x * tper;
-    const int64_t tend = tbeg + tper < ntile ? tbeg + tper : ntile;
+    // With at least one outer index per block, block b takes outer indices
+    // b, b + G, ... with all their chunks (the decode is reused across the
+    // chunks, and blocks running together cover one band of the tensors);
+    // otherwise the tiles are interleaved over the blocks.
+    const bool by_outer = d.nouter >= (int64_t)gridDim.x;
+    const int64_t nmine =
+        by_outer ? ((d.nouter - blockIdx.x + gridDim.x - 1) / gridDim.x) * nch
+                 : (ntile > blockIdx.x ? (ntile - blockIdx.x + gridDim.x - 1) / gridDim.x : 0);
     int64_t cur_o = -1, bx = 0, by = 0, bw = 0;
-    for (int64_t tile = tbeg; tile < tend; ++tile) {
-        int64_t crem;
-        const int64_t o = div_tile(tile, nch, lnch, crem);
+    for (int64_t k = 0; k < nmine; ++k) {
+        int64_t crem, o;
+        if (by_outer) {
+            const int64_t ko = div_tile(k, nch, lnch, crem);
+            o = (int64_t)blockIdx.x + ko * gridDim.x;
+        } else {
+            o = div_tile((int64_t)blockIdx.x + k * gridDim.x, nch, lnch, crem);
+        }
         const int c = (int)crem;
         if (o != cur_o) {
             cur_o = o;
@@ -194,16 +202,24 @@ __global__ void __launch_bounds__(256) k_absorb_sm(const __grid_constant__ ADesc
     const int nch = (nin + 256 * U - 1) / (256 * U);
     const int64_t ntile = d.nouter * nch;
     const int lnch = log2_if_pow2(nch);
-    // contiguous tile range per block; the outer decode is reused while the
-    // outer index stays the same
-    const int64_t tper = (ntile + gridDim.x - 1) / gridDim.x;
-    const int64_t tbeg = (int64_t)blockIdx.x * tper;
-    const int64_t tend = tbeg + tper < ntile ? tbeg + tper : ntile;
+    // With at least one outer index per block, block b takes outer indices
+    // b, b + G, ... with all their chunks (the decode is reused across the
+    // chunks, and blocks running together cover one band of the tensors);
+    // otherwise the tiles are interleaved over the blocks.
+    const bool by_outer = d.nouter >= (int64_t)gridDim.x;
+    const int64_t nmine =
+        by_outer ? ((d.nouter - blockIdx.x + gridDim.x - 1) / gridDim.x) * nch
+                 : (ntile > blockIdx.x ? (ntile - blockIdx.x + gridDim.x - 1) / gridDim.x : 0);
     int64_t cur_o = -1, bx = 0, by = 0;
     int cb = 0;
-    for (int64_t tile = tbeg; tile < tend; ++tile) {
-        int64_t crem;
-        const int64_t o = div_tile(tile, nch, lnch, crem);
+    for (int64_t k = 0; k < nmine; ++k) {
+        int64_t crem, o;
+        if (by_outer) {
+            const int64_t ko = div_tile(k, nch, lnch, crem);
+            o = (int64_t)blockIdx.x + ko * gridDim.x;
+        } else {
+            o = div_tile((int64_t)blockIdx.x + k * gridDim.x, nch, lnch, crem);
+        }
         const int c = (int)crem;
         if (o != cur_o) {
             cur_o = o;
