@@ -135,7 +135,12 @@ tn_status tn_tree_from_elimination(const tn_model *m, int nelim, const int *orde
  * over local rotations of the tree (objective: log2 of the total
  * multiply-add count plus a penalty on space complexity above the best seen
  * minus one), in the spirit of the tree-annealing finders the paper cites for
- * its orders (Sec. Tensor networks).  Host only; deterministic for a seed.
+ * its orders (Sec. Tensor networks); 3 = recursive bisection of the tensor
+ * hypergraph (one vertex per tensor, one hyperedge per variable weighted by
+ * log2 of its domain; Fiduccia-Mattheyses passes from max(4, restarts)
+ * random balanced starts per split), kept when it beats method 1's tree,
+ * followed by the annealing of method 2.
+ * Host only; deterministic for a seed.
  * Writes nleaves-1 entries to left/right. */
 tn_status tn_optimize_order(const tn_model *m, int method, int restarts, uint64_t seed,
                             int *left, int *right);

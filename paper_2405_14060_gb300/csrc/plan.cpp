@@ -635,10 +635,20 @@ Tree anneal_tree(const Net &net, const Tree &start, int iters, uint64_t seed, do
 
 Tree optimize_tree(const Net &net, int method, int restarts, uint64_t seed) {
     if (method == 0) return greedy_tree(net);
-    if (method == 2) {
-        // anneal from the best heuristic tree, restarts x 20000 rotations,
-        // first towards the smallest space complexity seen, then time
+    if (method == 2 || method == 3) {
+        // anneal from the best heuristic tree (method 2: elimination orders,
+        // method 3: recursive bisection), restarts x 20000 rotations, first
+        // towards the smallest space complexity seen, then time
         Tree t0 = optimize_tree(net, 1, std::max(2, restarts), seed);
+        if (method == 3) {
+            // the bisection tree when it beats the elimination heuristics
+            Tree tp = partition_tree(net, std::max(4, restarts), seed);
+            Plan pe, pp;
+            if (build_plan(net, tp, pp).empty() && build_plan(net, t0, pe).empty() &&
+                (pp.sc_log2 < pe.sc_log2 - 1e-9 ||
+                 (std::fabs(pp.sc_log2 - pe.sc_log2) < 1e-9 && pp.tc_log2 < pe.tc_log2)))
+                t0 = tp;
+        }
         Plan p0;
         build_plan(net, t0, p0);
         Tree best = t0;

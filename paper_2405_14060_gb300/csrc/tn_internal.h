@@ -62,6 +62,8 @@ std::string build_plan(const Net &net, const Tree &tree, Plan &plan, int64_t gem
 Tree greedy_tree(const Net &net);
 Tree tree_from_elimination(const Net &net, const std::vector<int> &order);
 Tree optimize_tree(const Net &net, int method, int restarts, uint64_t seed);
+// Tree from recursive bisection of the tensor hypergraph (order_part.cpp).
+Tree partition_tree(const Net &net, int starts, uint64_t seed);
 // Equivalent tree with runs of absorption steps re-associated (reassoc.cpp).
 Tree reassociate_chains(const Net &net, const Tree &tree);
 Tree anneal_tree(const Net &net, const Tree &start, int iters, uint64_t seed, double sc_target);

@@ -243,3 +243,27 @@ def test_choose_slices_reaches_target():
     # the current tree is used when none is given
     M.set_order(l, r)
     assert M.choose_slices(full["sc"] - 3, 8) == sl
+
+
+def test_partition_order_search():
+    """Recursive bisection (method 3, kept only where it beats the
+    elimination heuristics, then annealed): a valid tree, deterministic for a
+    seed, within two labels of the 12 x 12 grid's width, and never worse than
+    the elimination heuristics on a random 3-regular graph."""
+    m = synth.grid_ising(12, 5)
+    M = tn.Model.from_synth(m)
+    l1, r1 = M.optimize_order(3, 4, 9)
+    l2, r2 = M.optimize_order(3, 4, 9)
+    np.testing.assert_array_equal(l1, l2)
+    np.testing.assert_array_equal(r1, r2)
+    M.set_order(l1, r1)
+    st = M.tree_stats()
+    assert st["nodes"] == M.nleaves - 1
+    assert st["sc"] <= 12 + 2
+    # on a random 3-regular graph it does not lose to the elimination heuristics
+    m3 = synth.rrg3_ising(60, 7)
+    M3 = tn.Model.from_synth(m3)
+    M3.set_order(*M3.optimize_order(1, 8, 1))
+    sc1 = M3.tree_stats()["sc"]
+    M3.set_order(*M3.optimize_order(3, 4, 1))
+    assert M3.tree_stats()["sc"] <= sc1
