@@ -56,7 +56,7 @@ typedef enum {
     TN_E_OOM = 4,          /* device memory or the HBM budget exhausted */
     TN_E_CUDA = 5,         /* a CUDA call failed */
     TN_E_TIMEOUT = 6,      /* a bounded device-side wait gave up */
-    TN_E_UNSUPPORTED = 7   /* valid request outside what this build supports */
+    TN_E_UNSUPPORTED = 7   /* valid request outside what the library supports */
 } tn_status;
 
 typedef enum {

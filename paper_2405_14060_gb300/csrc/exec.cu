@@ -957,9 +957,9 @@ static void trace_program(const Program &P) {
                             (long long)a.rsy[k], (long long)a.rsw[k]);
             } else if (st.kind == 3) {
                 const RDesc &r = st.rd;
-                fprintf(stderr, "%s %d reduce ns %d nt %d ng %lld nm %lld nin %lld beta %d", dir,
-                        i, r.ns, r.nt, (long long)r.ng, (long long)r.nm, (long long)r.nin,
-                        r.nbeta);
+                fprintf(stderr, "%s %d reduce ns %d nt %d ng %lld nm %lld nin %lld beta %d vec %d",
+                        dir, i, r.ns, r.nt, (long long)r.ng, (long long)r.nm, (long long)r.nin,
+                        r.nbeta, (int)reduce_vector_form(r, P.esz));
                 fprintf(stderr, " xoff");
                 for (int k = 0; k < r.ns && k < 8; ++k) fprintf(stderr, ",%lld", (long long)r.xoff[k]);
                 fprintf(stderr, " zoff");

@@ -71,5 +71,7 @@ size_t reduce_scratch_bytes(const RDesc &d, int elem_bytes);
 template <typename T>
 void launch_reduce(const RDesc &d, void *scratch, cudaStream_t st);
 int reduce_launches(const RDesc &d);
+// Does the reduce run as k_reduce_vec (16-byte vector loads)?
+bool reduce_vector_form(const RDesc &d, int elem_bytes);
 
 }  // namespace tn
