@@ -47,7 +47,7 @@ UNIT = "solves/s"
 TRAFFIC = {
     "absorb": {"bytes_per_launch": 6.124e6, "launches": 272,
                "sources": {"paper_2405_14060_gb300/csrc/stream_impl.cuh":
-                           "e70105e4ac62d837ad12d8ccfa135767f3b74ed1abf506cd0bb621f14dd06e90",
+                           "03c7fe364243eef912e2ecd26c66b9ef81d20048b2117b87e2a1627fb842541a",
                            "paper_2405_14060_gb300/csrc/stream.cuh":
                            "0989adeb8b5a666f5824bedad209aca1f20b4f69416d16dabec4b4ee84b65512"}},
 }

@@ -1,6 +1,8 @@
-// Streaming contraction kernels, FP32 instantiations (see stream_impl.cuh).
+// Streaming contraction kernels, FP32 instantiations (see stream_impl.cuh and
+// reduce_impl.cuh).
 #define TN_STREAM_HOST_DEFS
 #include "stream_impl.cuh"
+#include "reduce_impl.cuh"
 
 namespace tn {
 template void launch_absorb<float>(const ADesc &, int, cudaStream_t);

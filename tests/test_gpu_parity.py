@@ -343,6 +343,13 @@ def test_workload2_full_size():
         assert abs(lz[0] - lz_ref) <= 1e-4 * abs(lz_ref), prec
         assert np.max(np.abs(marg - marg64)) < 1e-3, prec
         assert abs(M.pr(prec=prec)[0] - lz_ref) <= 1e-4 * abs(lz_ref), prec
+    # the split reductions sum their chunk partials in a fixed order: repeated
+    # solves agree bit for bit
+    for prec in ("tf32", "fp64"):
+        lza, ma = M.mar(prec=prec)
+        lzb, mb = M.mar(prec=prec)
+        np.testing.assert_array_equal(lza, lzb)
+        np.testing.assert_array_equal(ma, mb)
 
 
 def test_sampling_grid24_large_nodes():
