@@ -198,6 +198,21 @@ tn_status tn_pr(tn_model *m, int batch, const int32_t *evid, const tn_options *o
 tn_status tn_mar(tn_model *m, int batch, const int32_t *evid, const tn_options *opts,
                  double *logz, double *marg);
 
+/* Joint marginal of a set of variables Q = query[0..nq) (distinct, observed
+ * ones allowed): joint[q] = p(Q = q | e) over the joint domain of Q, row-major
+ * with the last query variable fastest (prod of their domain sizes entries,
+ * at most 65536), and logz = log p(e).  p(Q, e) is the contraction of the
+ * network with Q left open (Eq. evidence); the query labels are sliced and
+ * each slice -- the evidence extended by Q = q, a PR of Eq. pr -- is one row
+ * of a single batched contraction along the model's tree (sub-batched under
+ * the memory budget as tn_pr).  Assignments that contradict an observed
+ * query variable get 0 without being run.  In reduced precision the error
+ * of joint[q] follows the per-row log Z error.
+ * Errors: TN_E_ARG for a bad or repeated query variable, a joint domain
+ * above 65536 assignments, or p(e) = 0. */
+tn_status tn_joint_mar(tn_model *m, const int32_t *evid, int nq, const int32_t *query,
+                       const tn_options *opts, double *logz, double *joint);
+
 /* MPE: assign[nvars] maximises prod_f T_f given the evidence (observed
  * variables keep their value); logp = log of that maximum (Eq. log-map).
  * Ties go to the lowest flat index at each contraction.

@@ -247,6 +247,47 @@ def clamped_marginal(model, v: int, evid=None):
     return out
 
 
+def brute_joint_marginal(model, query, evid=None) -> np.ndarray:
+    """p(Q = q | e) for the variable set Q = query by summing the enumerated
+    joint of the free variables over the others (the definition of a
+    marginal); axes in the order of `query`.  Observed query variables take
+    probability 1 at their value."""
+    e = _ev(model, evid)
+    free = [v for v in range(len(e)) if e[v] < 0]
+    joint = brute_joint(model, e).reshape([int(model.card[v]) for v in free] or [1])
+    keep = [free.index(v) for v in query if e[v] < 0]
+    drop = tuple(i for i in range(len(free)) if i not in keep)
+    sub = joint.sum(axis=drop) if free else joint.reshape(())
+    # axes of `sub` follow increasing variable id; move them to query order
+    free_q = sorted(v for v in query if e[v] < 0)
+    if free_q:
+        sub = np.transpose(sub, [free_q.index(v) for v in query if e[v] < 0])
+    out = np.zeros([int(model.card[v]) for v in query])
+    idx = tuple(slice(None) if e[v] < 0 else int(e[v]) for v in query)
+    out[idx] = sub
+    return out
+
+
+def clamped_joint_marginal(model, query, evid=None) -> np.ndarray:
+    """p(Q = q | e) = Z(e, Q = q) / Z(e), each Z by bucket elimination
+    (Eq. mar-prob for a variable set, written out); axes in query order."""
+    e = _ev(model, evid).copy()
+    lz = ve_pr(model, e)
+    shape = [int(model.card[v]) for v in query]
+    out = np.zeros(shape)
+    for q in np.ndindex(*shape):
+        e2 = e.copy()
+        if any(e[v] >= 0 and e[v] != x for v, x in zip(query, q)):
+            continue
+        for v, x in zip(query, q):
+            e2[v] = x
+        try:
+            out[q] = np.exp(ve_pr(model, e2) - lz)
+        except ZeroDivisionError:
+            out[q] = 0.0
+    return out
+
+
 def split_marginals(model, flat):
     res, o = [], 0
     for c in model.card:

@@ -2544,6 +2544,67 @@ tn_status tn_mar_dev(tn_model *m, int batch, const int32_t *evid, const double *
                       grad);
 }
 
+// Joint marginal of a variable set Q: p(Q = q, e) is the contraction with Q
+// left open (Eq. evidence); with Q's labels sliced, each slice is the PR of
+// the evidence extended by Q = q (Eq. pr), so the slices run as the rows of
+// one batched PR along the model's tree.  Rows whose assignment contradicts
+// an observed query variable are not run (their probability is 0).
+static constexpr int64_t kJointMaxRows = 1 << 16;
+
+tn_status tn_joint_mar(tn_model *m, const int32_t *evid, int nq, const int32_t *query,
+                       const tn_options *opts, double *logz, double *joint) {
+    if (!m || nq < 1 || !query || !logz || !joint) return fail(TN_E_ARG, "bad argument");
+    const int nv = m->md.nvars;
+    if (nq > nv) return fail(TN_E_ARG, "more query variables than variables");
+    tn_status s = check_evid(m, 1, evid);
+    if (s) return s;
+    std::vector<char> seen(nv, 0);
+    int64_t rows = 1;
+    for (int i = 0; i < nq; ++i) {
+        const int v = query[i];
+        if (v < 0 || v >= nv) return fail(TN_E_ARG, "query variable out of range");
+        if (seen[v]) return fail(TN_E_ARG, "query variable " + std::to_string(v) + " repeated");
+        seen[v] = 1;
+        rows *= m->md.card[v];
+        if (rows > kJointMaxRows)
+            return fail(TN_E_ARG, "joint domain of the query holds more than 65536 assignments");
+    }
+    std::vector<int32_t> ev;
+    std::vector<int64_t> at;   // joint index of each batch row
+    std::vector<int32_t> row(nv);
+    for (int64_t r = 0; r < rows; ++r) {
+        for (int v = 0; v < nv; ++v) row[v] = evid ? evid[v] : -1;
+        bool ok = true;
+        int64_t x = r;
+        for (int i = nq - 1; i >= 0; --i) {   // the last query variable varies fastest
+            const int v = query[i], c = m->md.card[v];
+            const int32_t a = (int32_t)(x % c);
+            x /= c;
+            if (row[v] >= 0 && row[v] != a) ok = false;
+            row[v] = a;
+        }
+        if (!ok) continue;
+        ev.insert(ev.end(), row.begin(), row.end());
+        at.push_back(r);
+    }
+    std::fill(joint, joint + rows, 0.0);
+    std::vector<double> lz(at.size());
+    s = tn_pr(m, (int)at.size(), ev.data(), opts, lz.data());
+    if (s) return s;
+    // log p(e) = log sum_q p(Q = q, e)
+    double mx = -INFINITY;
+    for (double v : lz) mx = std::max(mx, v);
+    if (!(mx > -INFINITY)) {
+        *logz = -INFINITY;
+        return fail(TN_E_ARG, "p(e) = 0");
+    }
+    double sum = 0;
+    for (double v : lz) sum += std::exp(v - mx);
+    *logz = mx + std::log(sum);
+    for (size_t k = 0; k < at.size(); ++k) joint[at[k]] = std::exp(lz[k] - *logz);
+    return TN_OK;
+}
+
 tn_status tn_map(tn_model *m, const int32_t *evid, const tn_options *opts, int32_t *assign,
                  double *logp) {
     if (!m || !assign || !logp) return fail(TN_E_ARG, "bad argument");

@@ -24,7 +24,7 @@ EXPORTS = ["tn_load_model", "tn_load_model_arrays", "tn_free_model", "tn_set_ord
            "tn_mar", "tn_map", "tn_mmap", "tn_sample", "tn_pr_dev", "tn_mar_dev",
            "tn_last_device_ms", "tn_last_launch_count", "tn_last_error", "tn_contract_dev",
            "tn_profile", "tn_profile_steps", "tn_contract_dev_noalloc",
-           "tn_reassociate", "tn_choose_slices"]
+           "tn_reassociate", "tn_choose_slices", "tn_joint_mar"]
 PROFILE_CLASSES = ["small", "absorb", "reduce", "tcgemm", "simtgemm", "prep", "generic", "unused7"]
 
 
@@ -74,6 +74,7 @@ def lib():
             "tn_contract_dev_noalloc": [I, P, I, P, P, I, P, P, I, P, P, I, I, P, P],
             "tn_reassociate": [P, P, P, P, P],
             "tn_choose_slices": [P, P, P, D, I, P, P],
+            "tn_joint_mar": [P, P, I, P, P, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -245,6 +246,19 @@ class Model:
         o = _opts(prec, budget)
         _ck(lib().tn_mar(self._h, e.shape[0], _ptr(e), ctypes.byref(o), _ptr(lz), _ptr(marg)))
         return lz, marg
+
+    def joint_mar(self, query, evid=None, prec="fp64", budget=0):
+        """(log p(e), p(Q = q | e) as an array over the query's joint domain,
+        axes in the order of `query`)."""
+        e = self._evid(evid)
+        q = np.ascontiguousarray(query, np.int32)
+        shape = [int(self.card[v]) if 0 <= v < self.nvars else 1 for v in q] if q.size else [0]
+        out = np.zeros(int(np.prod(shape)))
+        lz = ctypes.c_double()
+        o = _opts(prec, budget)
+        _ck(lib().tn_joint_mar(self._h, _ptr(e[0]), len(q), _ptr(q), ctypes.byref(o),
+                               ctypes.byref(lz), _ptr(out)))
+        return lz.value, out.reshape(shape)
 
     def split(self, marg_row):
         out, p = [], 0

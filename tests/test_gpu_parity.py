@@ -75,6 +75,35 @@ def test_batched_evidence_matches_per_item():
     np.testing.assert_allclose(lz32, lz, rtol=1e-4)
 
 
+def test_joint_marginals_match_oracle():
+    """Joint marginals of variable sets (the query labels sliced into one
+    batched PR) against the oracle's enumeration, with an observed query
+    variable; an edge of a 160-spin tree Ising model against its closed form
+    exp(J s_i s_j) / (4 cosh J); argument errors."""
+    m = synth.random_markov(9, 12, 3, 8, cards=(2, 3, 4))
+    M = tn.Model.from_synth(m)
+    ev = np.full(m.nvars, -1, np.int32)
+    ev[4] = 1
+    lz_ref = oracle.brute_pr(m, ev)
+    for query in ([2], [0, 5], [7, 1, 3], [8, 4, 6]):
+        ref = oracle.brute_joint_marginal(m, query, ev)
+        for prec, tol in (("fp64", 1e-10), ("fp32", 1e-4)):
+            lz, P = M.joint_mar(query, ev, prec=prec)
+            assert P.shape == ref.shape
+            np.testing.assert_allclose(P, ref, rtol=0, atol=tol)
+            assert abs(lz - lz_ref) <= (1e-10 if prec == "fp64" else 1e-4 * max(1.0, abs(lz_ref)))
+    t = synth.tree_ising(160, 2)
+    T = tn.Model.from_synth(t)
+    i, j = (int(x) for x in t.scopes[17])
+    J = np.log(t.tables[17][3])
+    S = np.array([-1.0, 1.0])
+    _, P = T.joint_mar([i, j], prec="fp64")
+    np.testing.assert_allclose(P, np.exp(J * np.outer(S, S)) / (4 * np.cosh(J)), atol=1e-12)
+    for bad in ([2, 2], [m.nvars], []):
+        with pytest.raises(tn.TNError):
+            M.joint_mar(bad)
+
+
 def test_impossible_evidence():
     m = synth.chain_model(4, [2, 2, 2, 2], 1)
     m.tables[0] = np.array([0.0, 1.0])          # x0 = 0 has zero weight

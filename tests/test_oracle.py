@@ -242,6 +242,51 @@ def test_mmap_consistency_large():
             assert oracle.ve_pr(m, e3) <= lp + 1e-12
 
 
+# ------------------------------------------------------- joint marginals
+
+def test_joint_marginal_tree_ising_closed_form():
+    """Tree Ising without fields: an edge's pair marginal is
+    exp(J s_i s_j) / (4 cosh J), and two spins joined through k have
+    p(s_i, s_j) = (1 + s_i s_j tanh J_ik tanh J_kj) / 4 (closed forms)."""
+    m = synth.tree_ising(12, 5)
+    S = np.array([-1.0, 1.0])
+    nbr = {}
+    for sc, t in zip(m.scopes, m.tables):
+        i, j = (int(x) for x in sc)
+        J = np.log(t[3])
+        nbr.setdefault(i, {})[j] = J
+        nbr.setdefault(j, {})[i] = J
+        expect = np.exp(J * np.outer(S, S)) / (4 * np.cosh(J))
+        np.testing.assert_allclose(oracle.brute_joint_marginal(m, [i, j]), expect, atol=1e-12)
+        np.testing.assert_allclose(oracle.clamped_joint_marginal(m, [j, i]), expect.T, atol=1e-12)
+    k = next(v for v in nbr if len(nbr[v]) >= 2)
+    i, j = list(nbr[k])[:2]
+    t = np.tanh(nbr[k][i]) * np.tanh(nbr[k][j])
+    expect = (1 + t * np.outer(S, S)) / 4
+    np.testing.assert_allclose(oracle.brute_joint_marginal(m, [i, j]), expect, atol=1e-12)
+
+
+def test_joint_marginal_enumeration_matches_clamped_elimination():
+    """The enumeration route and the Bayes route (Z(e, Q = q) / Z(e) by
+    elimination) agree; single-variable sets give the marginals; observed
+    query variables put all mass on their value; every table sums to 1."""
+    m = synth.random_markov(9, 12, 3, 8, cards=(2, 3, 4))
+    ev = np.full(m.nvars, -1, np.int32)
+    ev[4] = 1
+    for query in ([2], [0, 5], [7, 1, 3], [3, 4], [8, 4, 6]):
+        a = oracle.brute_joint_marginal(m, query, ev)
+        b = oracle.clamped_joint_marginal(m, query, ev)
+        assert a.shape == tuple(int(m.card[v]) for v in query)
+        np.testing.assert_allclose(a, b, atol=1e-12)
+        assert abs(a.sum() - 1) < 1e-12
+        if 4 in query:
+            ax = query.index(4)
+            assert np.all(np.take(a, [x for x in range(int(m.card[4])) if x != 1], axis=ax) == 0)
+    _, marg = oracle.brute_mar(m, ev)
+    for v in (0, 2, 6):
+        np.testing.assert_allclose(oracle.brute_joint_marginal(m, [v], ev), marg[v], atol=1e-12)
+
+
 # ------------------------------------------------------------------ sampling
 
 def test_sampling_matches_joint():
