@@ -70,7 +70,7 @@ typedef struct {
     tn_prec prec;               /* default TN_FP64 */
     int64_t hbm_budget_bytes;   /* 0 = no limit beyond the device's memory */
     int max_slices;             /* reserved (slicing is set by tn_set_order) */
-    int autotune;               /* 1 = let the tile autotuner time candidates */
+    int autotune;               /* reserved (tile shapes are fixed per kernel family) */
     void *cuda_stream;          /* cudaStream_t for the _dev variants; NULL = default */
 } tn_options;                   /* a NULL options pointer means all defaults */
 
