@@ -18,6 +18,8 @@
  *          variable, then MPE over the query variables                (Sec. MMAP)
  *   - sampling: backward sampling through the cached contraction tree
  *          (Sec. "Generative modeling", Eq. sample, Eq. condition-prob)
+ *   - joint marginals p(Q | e) of a variable set: the contraction with Q
+ *          left open                                                  (Eq. evidence)
  *
  * Conventions
  *   - Variables are 0..nvars-1 with domain sizes card[v] >= 1.

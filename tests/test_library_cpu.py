@@ -49,6 +49,23 @@ def test_model_validation_errors():
         tn.Model.from_arrays([2, 2], [[0, 1]], [np.array([1.0, np.inf, 1.0, 1.0])])
 
 
+def test_joint_marginal_argument_errors():
+    """tn_joint_mar rejects a repeated or out-of-range query variable, an
+    empty query, evidence out of range and a joint domain above 65536
+    assignments before any device work (TN_E_ARG)."""
+    m = synth.grid_ising(5, 1)
+    M = tn.Model.from_synth(m)
+    ev = np.full(m.nvars, -1, np.int32)
+    for bad in ([3, 3], [m.nvars], [-1], [], list(range(17))):
+        with pytest.raises(tn.TNError) as e:
+            M.joint_mar(bad, ev)
+        assert e.value.status == 1, bad
+    ev[0] = 2
+    with pytest.raises(tn.TNError) as e:
+        M.joint_mar([1], ev)
+    assert e.value.status == 1
+
+
 def test_uai_roundtrip_and_parse_errors():
     m = synth.bayes_net(10, 3)
     with tempfile.TemporaryDirectory() as d:
