@@ -2308,7 +2308,7 @@ tn_status tn_tree_from_elimination(const tn_model *m, int nelim, const int *orde
 tn_status tn_optimize_order(const tn_model *m, int method, int restarts, uint64_t seed, int *left,
                             int *right) {
     if (!m || !left || !right) return fail(TN_E_ARG, "NULL argument");
-    if (method < 0 || method > 3) return fail(TN_E_ARG, "unknown method");
+    if (method < 0 || method > 4) return fail(TN_E_ARG, "unknown method");
     Tree t = optimize_tree(model_net(m->md, false), method, restarts, seed);
     std::copy(t.left.begin(), t.left.end(), left);
     std::copy(t.right.begin(), t.right.end(), right);

@@ -525,8 +525,10 @@ std::pair<double, double> sa_eval(SATree &T, std::vector<int> &post) {
 }
 }  // namespace
 
-Tree anneal_tree(const Net &net, const Tree &start, int iters, uint64_t seed, double sc_target) {
-    SATree T;
+namespace {
+// The annealer's state for a tree in tn_set_order's form (leaf bitsets set,
+// U and O of internal nodes still to be computed by sa_eval).
+void sa_init(const Net &net, const Tree &start, SATree &T) {
     T.nl = (int)net.leaf.size();
     int L = (int)net.card.size();
     T.W = (L + 63) / 64;
@@ -549,6 +551,46 @@ Tree anneal_tree(const Net &net, const Tree &start, int iters, uint64_t seed, do
     for (int v : net.out) T.outbits[v / 64] |= 1ull << (v % 64);
     for (int i = 0; i < T.nl; ++i)
         for (int v : net.leaf[i]) T.U[(size_t)i * T.W + v / 64] |= 1ull << (v % 64);
+}
+
+// The tree with children b0 / b1 (root 2 nl - 2) renumbered in post-order.
+Tree sa_renumber(int nl, const std::vector<int> &b0, const std::vector<int> &b1) {
+    const int NN = 2 * nl - 1;
+    Tree t;
+    t.nleaves = nl;
+    std::vector<int> id(NN, -1);
+    for (int i = 0; i < nl; ++i) id[i] = i;
+    std::vector<int> stack{NN - 1};
+    std::vector<char> seen(NN, 0);
+    std::vector<int> order;
+    while (!stack.empty()) {
+        int v = stack.back();
+        if (v < nl || seen[v]) {
+            stack.pop_back();
+            if (v >= nl) order.push_back(v);
+            continue;
+        }
+        seen[v] = 1;
+        stack.push_back(b1[v]);
+        stack.push_back(b0[v]);
+    }
+    int next = nl;
+    for (int v : order) id[v] = next++;
+    t.left.resize(nl - 1);
+    t.right.resize(nl - 1);
+    for (int v : order) {
+        int k = id[v] - nl;
+        t.left[k] = id[b0[v]];
+        t.right[k] = id[b1[v]];
+    }
+    return t;
+}
+}  // namespace
+
+Tree anneal_tree(const Net &net, const Tree &start, int iters, uint64_t seed, double sc_target) {
+    SATree T;
+    sa_init(net, start, T);
+    const int NN = 2 * T.nl - 1;
     std::vector<int> post;
     auto obj = [&](std::pair<double, double> r) {
         return r.first + 4.0 * std::max(0.0, r.second - sc_target);
@@ -602,39 +644,161 @@ Tree anneal_tree(const Net &net, const Tree &start, int iters, uint64_t seed, do
             T.par[y] = c;
         }
     }
-    // renumber the best tree in post-order
-    Tree t;
-    t.nleaves = T.nl;
-    std::vector<int> id(NN, -1);
-    for (int i = 0; i < T.nl; ++i) id[i] = i;
-    std::vector<int> stack{NN - 1};
-    std::vector<char> seen(NN, 0);
-    std::vector<int> order;
-    while (!stack.empty()) {
-        int v = stack.back();
-        if (v < T.nl || seen[v]) {
-            stack.pop_back();
-            if (v >= T.nl) order.push_back(v);
-            continue;
+    return sa_renumber(T.nl, b0, b1);
+}
+
+// The same rotations and objective, evaluated incrementally, with a colder
+// schedule (inverse temperature 10 -> 200: the many more moves would
+// otherwise wander far from the starting tree at the hot end).  Rotating
+// p(c(x, y), z) into p(c(x, z), y) keeps the leaf set under p, x, y and z, so
+// U of every node but c is unchanged, and so is O of x, y and z:
+// O(x) = U(y) | U(z) | O(p) before and after (likewise for y and z), hence
+// for all their descendants.  Only c's labels change, and with them only the
+// costs of c and p: a move costs a few bitset words instead of a pass over
+// the tree.  The sum of 2^cost is kept relative to a reference exponent (and
+// recomputed now and then against drift); the space term comes from a count
+// of node sizes.
+Tree anneal_tree_fast(const Net &net, const Tree &start, int64_t iters, uint64_t seed,
+                      double sc_target) {
+    SATree T;
+    sa_init(net, start, T);
+    const int NN = 2 * T.nl - 1, W = T.W, nl = T.nl;
+    std::vector<int> post;
+    sa_eval(T, post);
+    std::vector<uint64_t> Lb((size_t)NN * W);
+    for (size_t i = 0; i < Lb.size(); ++i) Lb[i] = T.U[i] & T.O[i];
+    auto Lof = [&](int v) { return &Lb[(size_t)v * W]; };
+    std::vector<uint64_t> tmp(W);
+    auto cost_of = [&](const uint64_t *a, const uint64_t *b) {
+        for (int w = 0; w < W; ++w) tmp[w] = a[w] | b[w];
+        return popw(tmp.data(), W, T.lw);
+    };
+    std::vector<double> cost(NN, 0.0), size(NN, 0.0);
+    auto key = [](double v) { return (int64_t)std::llround(v * 1048576.0); };
+    std::map<int64_t, int> sizes;   // node sizes (log2, fixed point) -> count
+    double ref = 0;
+    for (int v = nl; v < NN; ++v) {
+        cost[v] = cost_of(Lof(T.ch0[v]), Lof(T.ch1[v]));
+        size[v] = popw(Lof(v), W, T.lw);
+        sizes[key(size[v])]++;
+        ref = std::max(ref, cost[v]);
+    }
+    double S = 0;
+    auto resum = [&]() {
+        ref = 0;
+        for (int v = nl; v < NN; ++v) ref = std::max(ref, cost[v]);
+        S = 0;
+        for (int v = nl; v < NN; ++v) S += std::exp2(cost[v] - ref);
+    };
+    resum();
+    auto obj = [&](double Sv, double sc) {
+        return ref + std::log2(std::max(Sv, 1e-300)) + 4.0 * std::max(0.0, sc - sc_target);
+    };
+    auto sc_now = [&]() { return (double)sizes.rbegin()->first / 1048576.0; };
+    double fcur = obj(S, sc_now()), fbest = fcur;
+    std::vector<int> b0 = T.ch0, b1 = T.ch1;
+    std::mt19937_64 rng(seed);
+    std::uniform_real_distribution<double> U01(0, 1);
+    std::vector<uint64_t> nu(W), no(W), nlc(W);
+    int64_t since = 0;
+    for (int64_t it = 0; it < iters; ++it) {
+        const double beta = 10.0 + 190.0 * (double)it / (double)std::max<int64_t>(1, iters);
+        const int p = nl + (int)(rng() % (uint64_t)(nl - 1));
+        const int side = rng() & 1;
+        const int c = side ? T.ch1[p] : T.ch0[p];
+        if (c < nl) continue;
+        const int z = side ? T.ch0[p] : T.ch1[p];
+        const int pick = rng() & 1;
+        const int x = pick ? T.ch1[c] : T.ch0[c];   // stays under c
+        const int y = pick ? T.ch0[c] : T.ch1[c];   // moves up to p
+        const uint64_t *Ux = &T.U[(size_t)x * W], *Uy = &T.U[(size_t)y * W];
+        const uint64_t *Uz = &T.U[(size_t)z * W], *Op = &T.O[(size_t)p * W];
+        for (int w = 0; w < W; ++w) {
+            nu[w] = Ux[w] | Uz[w];
+            no[w] = Uy[w] | Op[w];
+            nlc[w] = nu[w] & no[w];
         }
-        seen[v] = 1;
-        stack.push_back(b1[v]);
-        stack.push_back(b0[v]);
+        const double cc = cost_of(Lof(x), Lof(z)), cp = cost_of(nlc.data(), Lof(y));
+        const double sz = popw(nlc.data(), W, T.lw);
+        const double Sn = S - std::exp2(cost[c] - ref) - std::exp2(cost[p] - ref) +
+                          std::exp2(cc - ref) + std::exp2(cp - ref);
+        // space term with size[c] replaced by sz
+        const int64_t ko = key(size[c]), kn = key(sz);
+        double scn;
+        {
+            auto top = sizes.rbegin();
+            if (kn >= top->first) scn = sz;
+            else if (ko == top->first && top->second == 1) {
+                auto nx = std::next(top);
+                int64_t k2 = nx == sizes.rend() ? kn : std::max(kn, nx->first);
+                scn = (double)k2 / 1048576.0;
+            } else scn = (double)top->first / 1048576.0;
+        }
+        const double fn = obj(Sn, scn);
+        if (!(fn <= fcur || U01(rng) < std::exp(-beta * (fn - fcur)))) continue;
+        // accept: c = (x, z), p = (c, y)
+        T.ch0[c] = x;
+        T.ch1[c] = z;
+        T.par[z] = c;
+        if (side) T.ch0[p] = y;
+        else T.ch1[p] = y;
+        T.par[y] = p;
+        std::copy(nu.begin(), nu.end(), T.U.begin() + (size_t)c * W);
+        std::copy(no.begin(), no.end(), T.O.begin() + (size_t)c * W);
+        std::copy(nlc.begin(), nlc.end(), Lb.begin() + (size_t)c * W);
+        if (--sizes[ko] == 0) sizes.erase(ko);
+        sizes[kn]++;
+        size[c] = sz;
+        cost[c] = cc;
+        cost[p] = cp;
+        S = Sn;
+        if (++since >= 4096 || !(S > 1e-200)) {
+            resum();
+            since = 0;
+        }
+        fcur = obj(S, sc_now());
+        if (fcur < fbest - 1e-12) {
+            fbest = fcur;
+            b0 = T.ch0;
+            b1 = T.ch1;
+        }
     }
-    int next = T.nl;
-    for (int v : order) id[v] = next++;
-    t.left.resize(T.nl - 1);
-    t.right.resize(T.nl - 1);
-    for (int v : order) {
-        int k = id[v] - T.nl;
-        t.left[k] = id[b0[v]];
-        t.right[k] = id[b1[v]];
-    }
-    return t;
+    return sa_renumber(nl, b0, b1);
 }
 
 Tree optimize_tree(const Net &net, int method, int restarts, uint64_t seed) {
     if (method == 0) return greedy_tree(net);
+    if (method == 4) {
+        // the better of method 1's tree and the bisection tree, then
+        // `restarts` rounds of incremental annealing (2000 rotations per
+        // leaf each), each from the best tree so far
+        Tree best = optimize_tree(net, 1, std::max(2, restarts), seed);
+        Plan pb;
+        if (!build_plan(net, best, pb).empty()) return best;
+        {
+            Tree tp = partition_tree(net, std::max(4, restarts), seed);
+            Plan pp;
+            if (build_plan(net, tp, pp).empty() &&
+                (pp.sc_log2 < pb.sc_log2 - 1e-9 ||
+                 (std::fabs(pp.sc_log2 - pb.sc_log2) < 1e-9 && pp.tc_log2 < pb.tc_log2))) {
+                best = tp;
+                pb = pp;
+            }
+        }
+        double bsc = pb.sc_log2, btc = pb.tc_log2;
+        const int64_t iters = 2000LL * (int64_t)net.leaf.size();
+        for (int r = 0; r < std::max(1, restarts); ++r) {
+            Tree t = anneal_tree_fast(net, best, iters, seed + 7919 * (r + 1), bsc - 1.0);
+            Plan p;
+            if (!build_plan(net, t, p).empty()) continue;
+            if (p.sc_log2 < bsc - 1e-9 || (std::fabs(p.sc_log2 - bsc) < 1e-9 && p.tc_log2 < btc)) {
+                best = t;
+                bsc = p.sc_log2;
+                btc = p.tc_log2;
+            }
+        }
+        return best;
+    }
     if (method == 2 || method == 3) {
         // anneal from the best heuristic tree (method 2: elimination orders,
         // method 3: recursive bisection), restarts x 20000 rotations, first

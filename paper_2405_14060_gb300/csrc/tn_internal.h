@@ -67,6 +67,9 @@ Tree partition_tree(const Net &net, int starts, uint64_t seed);
 // Equivalent tree with runs of absorption steps re-associated (reassoc.cpp).
 Tree reassociate_chains(const Net &net, const Tree &tree);
 Tree anneal_tree(const Net &net, const Tree &start, int iters, uint64_t seed, double sc_target);
+// The same annealing, evaluated incrementally (a move updates one node).
+Tree anneal_tree_fast(const Net &net, const Tree &start, int64_t iters, uint64_t seed,
+                      double sc_target);
 double log2_size(const Net &net, const Labels &l);
 
 }  // namespace tn
