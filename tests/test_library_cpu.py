@@ -288,6 +288,19 @@ def test_incremental_annealing_order_search():
     assert s4["tc"] <= s2["tc"] - 3
 
 
+def test_order_search_on_tiny_models():
+    """Every order-search method returns a valid tree for networks of two,
+    three and five leaves (a single factor over one variable upwards)."""
+    cases = (([2], [[0]], [np.array([1.0, 2.0])]),
+             ([3, 2], [[0, 1]], [np.arange(1, 7, dtype=float)]),
+             ([2, 2, 2], [[0, 1], [1, 2]], [np.ones(4), np.ones(4)]))
+    for card, scopes, tables in cases:
+        M = tn.Model.from_arrays(card, scopes, tables)
+        for method in range(5):
+            M.set_order(*M.optimize_order(method, 3, 0))
+            assert M.tree_stats()["nodes"] == M.nleaves - 1
+
+
 def test_partition_order_search():
     """Recursive bisection (method 3, kept only where it beats the
     elimination heuristics, then annealed): a valid tree, deterministic for a
