@@ -78,7 +78,7 @@ typedef struct {
 
 /* ------------------------------------------------------------ model */
 
-/* Parse a UAI-format MARKOV or BAYES file (Sec. Benchmarks uses the UAI
+/* Parse a UAI-format MARKOV or BAYES file (Sec. "Performance benchmarks" uses the UAI
  * competition format).  *out receives a new model (free with tn_free_model).
  * Errors: TN_E_ARG (NULL arguments, unreadable file), TN_E_PARSE. */
 tn_status tn_load_model(const char *uai_path, tn_model **out);

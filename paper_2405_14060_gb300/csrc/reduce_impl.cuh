@@ -1,7 +1,7 @@
 // Streaming reductions of two big tensors to a small one (the B-bar =
-// con(A, C-bar) steps of the adjoint sweep and forward nodes whose result is
-// small; paper Sec. "Tensor networks", Eq. adjoint rule).  Both big operands
-// are read from HBM exactly once:
+// con(A, C-bar) steps of the adjoint sweep, Thm. "Tensor network
+// differentiation", Eq. einback, and forward nodes whose result is small).
+// Both big operands are read from HBM exactly once:
 //
 //   k_reduce_part  each block streams a chunk of the summed positions m of one
 //                  group g and accumulates the outer products X[g,m,s] Z[g,m,t]
