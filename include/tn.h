@@ -325,8 +325,9 @@ tn_status tn_contract_dev(int nlabels, const int *sizes,
 
 /*
  * The same pairwise contraction as tn_contract_dev (same arguments, same
- * results up to floating-point summation order), always on the split-K
- * strided kernels, without allocating any device memory.  The paper has no
+ * results up to floating-point summation order), on the strided contraction
+ * kernels (split over the summed space where it is long, one pass per output
+ * entry otherwise), without allocating any device memory.  The paper has no
  * counterpart: this entry point exists for callers that cannot let a library
  * allocate GPU memory -- an application that owns all device memory through
  * its own pool, or a latency-critical loop where cudaMalloc / cudaFree, which
@@ -334,9 +335,8 @@ tn_status tn_contract_dev(int nlabels, const int *sizes,
  *
  * The split-K partial sums live in one file-scope device array of
  * TN_NOALLOC_SCRATCH_BYTES bytes that every GPU loading the library holds
- * until the process exits.  An output whose partials cannot fit even with a
- * single K chunk per output entry (more than TN_NOALLOC_SCRATCH_BYTES /
- * (element size + 4) entries) is rejected with TN_E_ARG and a message naming
+ * until the process exits.  An output of more than TN_NOALLOC_SCRATCH_BYTES /
+ * (element size + 4) entries is rejected with TN_E_ARG and a message naming
  * the limit; nothing is launched then.
  *
  * The first call on each device looks up the array's device address (once,
@@ -347,7 +347,7 @@ tn_status tn_contract_dev(int nlabels, const int *sizes,
  * -- on different streams without ordering, or from several host threads --
  * race on the array and must be serialised by the caller.  The call
  * synchronises `cuda_stream` before returning.  prec is not taken: the
- * split-K kernels compute in the data type (dtype 0 double, 1 float).
+ * contraction kernels compute in the data type (dtype 0 double, 1 float).
  */
 tn_status tn_contract_dev_noalloc(int nlabels, const int *sizes,
                                   int na, const int *labels_a, const void *A,

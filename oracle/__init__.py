@@ -99,6 +99,13 @@ def num_threads() -> int:
     return int(_load().or_num_threads())
 
 
+def set_num_threads(n: int) -> None:
+    """Number of OpenMP threads the following oracle calls use."""
+    L = _load()
+    L.or_set_num_threads.restype = None
+    L.or_set_num_threads(ctypes.c_int(int(n)))
+
+
 # ------------------------------------------------------------ brute force
 
 def brute_pr(model, evid=None) -> float:
@@ -231,17 +238,19 @@ def log_weight(model, x) -> float:
     return float(_load().or_log_weight(*m.args(), _p(xa)))
 
 
-def clamped_marginal(model, v: int, evid=None):
+def clamped_marginal(model, v: int, evid=None, order=None, logz=None):
     """p(v = x | e) for every x by conditioning: Z(e, v=x) / Z(e), each by
-    bucket elimination (Eq. mar-prob written out)."""
+    bucket elimination (Eq. mar-prob written out).  ``order`` (optional) is
+    the elimination order of every call (observed variables are skipped);
+    ``logz`` (optional) is log Z(e) when already known."""
     e = _ev(model, evid).copy()
-    lz = ve_pr(model, e)
+    lz = ve_pr(model, e, order) if logz is None else float(logz)
     out = np.zeros(int(model.card[v]))
     for x in range(int(model.card[v])):
         e2 = e.copy()
         e2[v] = x
         try:
-            out[x] = np.exp(ve_pr(model, e2) - lz)
+            out[x] = np.exp(ve_pr(model, e2, order) - lz)
         except ZeroDivisionError:
             out[x] = 0.0
     return out

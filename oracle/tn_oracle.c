@@ -1195,3 +1195,12 @@ int or_num_threads(void) {
     return 1;
 #endif
 }
+
+/* Threads used by later calls (timing single-threaded and on all cores). */
+void or_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}

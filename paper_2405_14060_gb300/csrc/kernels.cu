@@ -293,29 +293,29 @@ void launch_contract(const CDesc &d, int semiring, void *scratch, size_t scratch
     if (nlaunch) *nlaunch += 1;
 }
 
-// Split-K contraction into a fixed scratch buffer of `cap` bytes: the number
-// of K chunks is the one launch_contract would pick, lowered until the
-// partial results fit.  Returns false (launching nothing) when even one chunk
-// per output does not fit.
+// Contraction with any scratch in a fixed buffer of `cap` bytes: outputs
+// whose summed space is long enough for split-K (the choice launch_contract
+// makes) keep their partial results there, the others run on k_contract,
+// which needs no scratch.  The K-chunk count of split-K is bounded so that
+// outputs x chunks stay near kTargetThreads / 256, hence its partials hold at
+// most a few thousand entries.  Returns false (launching nothing) when the
+// output has more than cap / (element size + 4) entries, the limit stated for
+// callers whatever the path.
 template <typename T>
 bool launch_contract_splitk_fixed(const CDesc &d, int semiring, void *scratch, size_t cap,
                                   cudaStream_t st) {
     int64_t total = d.nout_total * d.nbeta;
     if (total == 0) return true;
+    if ((size_t)total * (sizeof(T) + 4) > cap) return false;
+    if (!use_splitk(d)) {
+        launch_contract<T>(d, semiring, nullptr, 0, st, nullptr);
+        return true;
+    }
     int64_t chunk;
     int nchunks;
     splitk_shape(d, chunk, nchunks);
-    auto need = [&](int nc) {
-        size_t pb = ((size_t)(total * nc) * sizeof(T) + 255) & ~(size_t)255;
-        return pb + (size_t)(total * nc) * 4;
-    };
-    while (nchunks > 1 && need(nchunks) > cap) {
-        nchunks = (nchunks + 1) / 2;
-        chunk = (d.ktotal + nchunks - 1) / nchunks;
-        nchunks = (int)((d.ktotal + chunk - 1) / chunk);
-    }
-    if (need(nchunks) > cap) return false;
     size_t pb = ((size_t)(total * nchunks) * sizeof(T) + 255) & ~(size_t)255;
+    if (pb + (size_t)(total * nchunks) * 4 > cap) return false;
     T *part = (T *)scratch;
     int32_t *pidx = (int32_t *)((char *)scratch + pb);
     dim3 grid((unsigned)nchunks, (unsigned)std::min<int64_t>(total, 65535),

@@ -4,9 +4,10 @@
 // owns all device memory through its own pool and forbids other allocations,
 // or a latency-critical loop where cudaMalloc / cudaFree (which may
 // synchronise the whole device) are not acceptable.  For them,
-// tn_contract_dev_noalloc runs the split-K contraction kernels of
-// tn_contract_dev with their partial sums in one fixed-size array that lives
-// in the library's device image instead of in allocated memory.
+// tn_contract_dev_noalloc runs the strided contraction kernels of
+// tn_contract_dev, keeping the partial sums of the split-K form in one
+// fixed-size array that lives in the library's device image instead of in
+// allocated memory.
 #include <mutex>
 #include <string>
 

@@ -344,15 +344,43 @@ class Model:
         return int(lib().tn_last_launch_count(self._h))
 
 
-def contract_dev(sizes, la, A, lb, B, lc, C, semiring=0, argmax=None, prec="fp32",
-                 stream=None):
-    """One pairwise contraction on torch CUDA tensors (float64 or float32)."""
+def _contract_args(sizes, la, A, lb, B, lc, C, argmax):
+    """Checks shared by the pairwise-contraction bindings: A, B and C are
+    contiguous CUDA tensors on the current device with one dtype (float64 or
+    float32) and the entry counts their labels give; argmax, when given, is a
+    contiguous int32 CUDA tensor with one entry per output entry."""
     import torch
-    dtype = 0 if A.dtype == torch.float64 else 1
     sz = np.ascontiguousarray(sizes, np.int32)
     a = np.ascontiguousarray(la, np.int32)
     b = np.ascontiguousarray(lb, np.int32)
     c = np.ascontiguousarray(lc, np.int32)
+    if A.dtype not in (torch.float64, torch.float32):
+        raise TNError(1, "A must be float64 or float32")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    for name, t in (("A", A), ("B", B), ("C", C)):
+        if t.dtype != A.dtype:
+            raise TNError(1, f"{name} has dtype {t.dtype}, A has {A.dtype}")
+        if t.device != dev or not t.is_contiguous():
+            raise TNError(1, f"{name} must be a contiguous tensor on {dev}")
+    for name, t, l in (("A", A, a), ("B", B, b), ("C", C, c)):
+        if np.any(l < 0) or np.any(l >= len(sz)):
+            raise TNError(1, f"label of {name} out of range")
+        want = int(np.prod([int(sz[v]) for v in l])) if len(l) else 1
+        if t.numel() != want:
+            raise TNError(1, f"{name} has {t.numel()} entries, its labels give {want}")
+    if argmax is not None:
+        if (argmax.dtype != torch.int32 or argmax.device != dev or
+                not argmax.is_contiguous() or argmax.numel() != C.numel()):
+            raise TNError(1, "argmax must be a contiguous int32 tensor with one entry "
+                             "per output entry on the current device")
+    dtype = 0 if A.dtype == torch.float64 else 1
+    return sz, a, b, c, dtype
+
+
+def contract_dev(sizes, la, A, lb, B, lc, C, semiring=0, argmax=None, prec="fp32",
+                 stream=None):
+    """One pairwise contraction on torch CUDA tensors (float64 or float32)."""
+    sz, a, b, c, dtype = _contract_args(sizes, la, A, lb, B, lc, C, argmax)
     _ck(lib().tn_contract_dev(len(sz), _ptr(sz), len(a), _ptr(a), A.data_ptr(), len(b), _ptr(b),
                               B.data_ptr(), len(c), _ptr(c) if len(c) else None, C.data_ptr(),
                               semiring, dtype, PRECS[prec],
@@ -362,12 +390,7 @@ def contract_dev(sizes, la, A, lb, B, lc, C, semiring=0, argmax=None, prec="fp32
 def contract_dev_noalloc(sizes, la, A, lb, B, lc, C, semiring=0, argmax=None, stream=None):
     """tn_contract_dev_noalloc: the same contraction as contract_dev without
     any device allocation (split-K partials in the library's fixed scratch)."""
-    import torch
-    dtype = 0 if A.dtype == torch.float64 else 1
-    sz = np.ascontiguousarray(sizes, np.int32)
-    a = np.ascontiguousarray(la, np.int32)
-    b = np.ascontiguousarray(lb, np.int32)
-    c = np.ascontiguousarray(lc, np.int32)
+    sz, a, b, c, dtype = _contract_args(sizes, la, A, lb, B, lc, C, argmax)
     _ck(lib().tn_contract_dev_noalloc(len(sz), _ptr(sz), len(a), _ptr(a), A.data_ptr(), len(b),
                                       _ptr(b), B.data_ptr(), len(c), _ptr(c) if len(c) else None,
                                       C.data_ptr(), semiring, dtype,
