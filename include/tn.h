@@ -306,7 +306,10 @@ const char *tn_last_error(void);
  * and summed label groups each hold at least 64 entries (and with no label
  * summed inside one operand alone) runs as a batched GEMM: TN_TF32 / TN_BF16
  * on tcgen05 tensor cores (float data only), TN_FP32 / TN_FP64 on a CUDA-core
- * tiled GEMM; everything else runs on the strided contraction kernels.  No
+ * tiled GEMM; other sum-product contractions with no label summed inside one
+ * operand run on a batched strided GEMM over the label groups (CUDA cores,
+ * operands read in place through per-group offset tables); everything else
+ * runs on the strided contraction kernels.  No
  * rescaling is applied.  The call allocates its scratch memory (operand
  * workspaces, split-K partial sums) stream-ordered from the CUDA memory pool
  * and synchronises `cuda_stream` before returning.

@@ -21,6 +21,7 @@
 #include <tuple>
 #include <vector>
 
+#include "bgemm.cuh"
 #include "gemm.cuh"
 #include "kernels.cuh"
 #include "micro.cuh"
@@ -116,7 +117,7 @@ enum Kind { K_PR = 0, K_MAR = 1, K_MAP = 2, K_SAMPLE = 3, K_SUMNET = 4, K_MAXNET
 
 // Kernel classes for profiling.
 enum Cls { C_SMALL = 0, C_STREAM = 1, C_SPLITK = 2, C_TCGEMM = 3, C_SIMTGEMM = 4, C_PREP = 5,
-           C_GENERIC = 6, C_NCLS = 8 };
+           C_GENERIC = 6, C_BGEMM = 7, C_NCLS = 8 };
 
 struct GemmOp {
     PDesc px, py, post;
@@ -130,12 +131,15 @@ struct GemmOp {
 };
 
 struct Step {
-    int kind = 0;          // 0: strided contraction, 1: GEMM form, 2: absorb, 3: reduce
+    int kind = 0;          // 0: strided contraction, 1: GEMM form, 2: absorb, 3: reduce,
+                           // 4: batched strided GEMM
     int semiring = 0;
     CDesc d;
     GemmOp g;
     ADesc ad;
     RDesc rd;
+    BDesc bd;
+    std::vector<int32_t> btab;     // offset tables of a batched strided GEMM (host copy)
     double flops = 0, bytes = 0;   // algorithmic: 2 * multiply-adds; operands + result once
     const char *why = "";          // why a strided contraction did not stream (plan trace)
     int node = -1;                 // the tensor this step writes: fwd[node] or adj[node]
@@ -848,6 +852,120 @@ static bool make_reduce(const std::vector<int> &card, const Labels &lx, bool bx,
     return true;
 }
 
+// Batched strided GEMM: O[g, m, n] = sum_k X[g, m, k] Y[g, k, n] with the
+// label groups G (in X, Y and O), M (X and O), N (Y and O) and K (X and Y),
+// each label of O, X and Y in exactly one group (no label summed inside one
+// operand).  The side with more row entries goes to M.  Writes the offset
+// tables, in the order the descriptor's table pointers take them, to `tab`.
+static bool make_bgemm(const std::vector<int> &card, const Labels &lx, bool bx, int64_t perx,
+                       const void *X, const unsigned long long *mxx, const Labels &ly, bool by,
+                       int64_t pery, const void *Y, const unsigned long long *mxy,
+                       const Labels &lo, bool bo, int64_t pero, void *O,
+                       unsigned long long *mxo, int nbeta, int esz, BDesc &d,
+                       std::vector<int32_t> &tab, bool swapped = false) {
+    std::memset(&d, 0, sizeof d);
+    if (bo != (bx || by)) return false;
+    std::set<int> sx(lx.begin(), lx.end()), sy(ly.begin(), ly.end()), so(lo.begin(), lo.end());
+    Labels G, M, N, K;
+    for (int v : lx) {
+        bool iy = sy.count(v), io = so.count(v);
+        if (iy && io) G.push_back(v);
+        else if (io) M.push_back(v);
+        else if (iy) K.push_back(v);
+        else return false;
+    }
+    for (int v : ly) {
+        bool ix = sx.count(v), io = so.count(v);
+        if (ix) continue;
+        if (io) N.push_back(v);
+        else return false;
+    }
+    for (int v : lo)
+        if (!sx.count(v) && !sy.count(v)) return false;
+    auto prod = [&](const Labels &l) {
+        int64_t p = 1;
+        for (int v : l) p *= card[v];
+        return p;
+    };
+    d.G = prod(G);
+    d.M = prod(M);
+    d.N = prod(N);
+    d.K = prod(K);
+    if (!swapped && d.N > d.M)
+        return make_bgemm(card, ly, by, pery, Y, mxy, lx, bx, perx, X, mxx, lo, bo, pero, O, mxo,
+                          nbeta, esz, d, tab, true);
+    if (perx >= (1LL << 31) || pery >= (1LL << 31) || pero >= (1LL << 31)) return false;
+    const int64_t ntab = 3 * d.G + 2 * d.M + 2 * d.N + 2 * d.K;
+    if (ntab > (1LL << 26)) return false;
+    tab.assign((size_t)ntab, 0);
+    // offsets of every index of a group (labels in the given order, last
+    // fastest) in one tensor
+    auto fill = [&](const Labels &grp, const Labels &lt, const std::set<int> &st, int32_t *out) {
+        int64_t tot = prod(grp);
+        std::vector<int64_t> sz, sd;
+        for (int v : grp) {
+            sz.push_back(card[v]);
+            sd.push_back(st.count(v) ? stride_in(card, lt, v) : 0);
+        }
+        std::vector<int64_t> dig(grp.size(), 0);
+        int64_t off = 0;
+        for (int64_t i = 0; i < tot; ++i) {
+            out[i] = (int32_t)off;
+            for (int k = (int)grp.size() - 1; k >= 0; --k) {
+                off += sd[k];
+                if (++dig[k] < sz[k]) break;
+                off -= sd[k] * sz[k];
+                dig[k] = 0;
+            }
+        }
+    };
+    int32_t *t = tab.data();
+    int64_t p = 0;
+    int64_t o_ag = p; fill(G, lx, sx, t + p); p += d.G;
+    int64_t o_bg = p; fill(G, ly, sy, t + p); p += d.G;
+    int64_t o_cg = p; fill(G, lo, so, t + p); p += d.G;
+    int64_t o_am = p; fill(M, lx, sx, t + p); p += d.M;
+    int64_t o_cm = p; fill(M, lo, so, t + p); p += d.M;
+    int64_t o_bn = p; fill(N, ly, sy, t + p); p += d.N;
+    int64_t o_cn = p; fill(N, lo, so, t + p); p += d.N;
+    int64_t o_ak = p; fill(K, lx, sx, t + p); p += d.K;
+    int64_t o_bk = p; fill(K, ly, sy, t + p); p += d.K;
+    // table pointers hold offsets into the table until the buffer is placed
+    d.tag = (const int32_t *)(intptr_t)o_ag;
+    d.tbg = (const int32_t *)(intptr_t)o_bg;
+    d.tcg = (const int32_t *)(intptr_t)o_cg;
+    d.tam = (const int32_t *)(intptr_t)o_am;
+    d.tcm = (const int32_t *)(intptr_t)o_cm;
+    d.tbn = (const int32_t *)(intptr_t)o_bn;
+    d.tcn = (const int32_t *)(intptr_t)o_cn;
+    d.tak = (const int32_t *)(intptr_t)o_ak;
+    d.tbk = (const int32_t *)(intptr_t)o_bk;
+    // the group holding each tensor's fastest label (of size > 1)
+    auto fastest = [&](const Labels &lt) {
+        for (int k = (int)lt.size() - 1; k >= 0; --k)
+            if (card[lt[k]] > 1) return lt[k];
+        return -1;
+    };
+    auto in = [](const Labels &l, int v) { return std::find(l.begin(), l.end(), v) != l.end(); };
+    d.a_kfast = in(K, fastest(lx)) ? 1 : 0;
+    d.b_kfast = in(K, fastest(ly)) ? 1 : 0;
+    d.c_nfast = in(N, fastest(lo)) ? 1 : 0;
+    d.nbeta = bo ? nbeta : 1;
+    d.bsa = (bo && bx) ? perx : 0;
+    d.bsb = (bo && by) ? pery : 0;
+    d.bsc = bo ? pero : 0;
+    d.A = X;
+    d.B = Y;
+    d.C = O;
+    d.mxa = mxx;
+    d.mxb = mxy;
+    d.mxa_bs = bx ? 1 : 0;
+    d.mxb_bs = by ? 1 : 0;
+    d.mxc = mxo;
+    bgemm_configure(d, esz);
+    return true;
+}
+
 static bool to_micro(const CDesc &d, const char *arena, int esz, const unsigned long long *mxb,
                      const int32_t *amb, MicroDesc &m) {
     std::memset(&m, 0, sizeof m);
@@ -982,6 +1100,13 @@ static void trace_program(const Program &P) {
                 pd("px", st.g.px);
                 pd("py", st.g.py);
                 if (st.g.has_post) pd("post", st.g.post);
+            }
+            else if (st.kind == 4) {
+                const BDesc &b = st.bd;
+                fprintf(stderr, "%s %d bgemm g %lld m %lld n %lld k %lld beta %d split %d tile %d "
+                        "kfast %d/%d nfast %d", dir, i, (long long)b.G, (long long)b.M,
+                        (long long)b.N, (long long)b.K, b.nbeta, b.nsplit, b.tile, b.a_kfast,
+                        b.b_kfast, b.c_nfast);
             }
             else
                 fprintf(stderr, "%s %d contract outs %lld k %lld [%s]", dir, i,
@@ -1312,6 +1437,14 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                        st.rd.nm >= 4096) {
                 st.kind = 3;
                 scratch = std::max(scratch, reduce_scratch_bytes(st.rd, P.esz));
+            } else if (!maxplus &&
+                       make_bgemm(net.card, na.labels, na.beta, P.fwd[nd.a].per, fptr(nd.a),
+                                  mxp(P.fwd[nd.a].mx), nb.labels, nb.beta, P.fwd[nd.b].per,
+                                  fptr(nd.b), mxp(P.fwd[nd.b].mx), nd.labels, nd.beta,
+                                  P.fwd[id].per, fptr(id), mxp(P.fwd[id].mx), nbeta, P.esz, st.bd,
+                                  st.btab)) {
+                st.kind = 4;
+                scratch = std::max(scratch, bgemm_scratch_bytes(st.bd, P.esz));
             } else {
                 st.kind = 0;
                 st.d = d;
@@ -1374,6 +1507,13 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                                 P.adj[nd.a].per, aptr(nd.a), P.mx + P.adj[nd.a].mx, nullptr, nbeta,
                                 nullptr, st.ad)) {
                     st.kind = 2;
+                } else if (make_bgemm(net.card, nd.labels, P.adj_beta[id], P.adj[id].per, cbar,
+                                      P.mx + P.adj[id].mx, nb.labels, nb.beta, P.fwd[nd.b].per,
+                                      fptr(nd.b), P.mx + P.fwd[nd.b].mx, na.labels,
+                                      P.adj_beta[nd.a], P.adj[nd.a].per, aptr(nd.a),
+                                      P.mx + P.adj[nd.a].mx, nbeta, P.esz, st.bd, st.btab)) {
+                    st.kind = 4;
+                    scratch = std::max(scratch, bgemm_scratch_bytes(st.bd, P.esz));
                 } else {
                     err = make_desc(net.card, nd.labels, P.adj_beta[id], P.adj[id].per, cbar,
                                     P.mx + P.adj[id].mx, nb.labels, nb.beta, P.fwd[nd.b].per,
@@ -1413,6 +1553,13 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                     st.rd.nm >= 4096) {
                     st.kind = 3;
                     scratch = std::max(scratch, reduce_scratch_bytes(st.rd, P.esz));
+                } else if (make_bgemm(net.card, na.labels, na.beta, P.fwd[nd.a].per, fptr(nd.a),
+                                      P.mx + P.fwd[nd.a].mx, nd.labels, P.adj_beta[id],
+                                      P.adj[id].per, cbar, P.mx + P.adj[id].mx, nb.labels,
+                                      P.adj_beta[nd.b], P.adj[nd.b].per, aptr(nd.b),
+                                      P.mx + P.adj[nd.b].mx, nbeta, P.esz, st.bd, st.btab)) {
+                    st.kind = 4;
+                    scratch = std::max(scratch, bgemm_scratch_bytes(st.bd, P.esz));
                 } else {
                     err = make_desc(net.card, na.labels, na.beta, P.fwd[nd.a].per, fptr(nd.a),
                                     P.mx + P.fwd[nd.a].mx, nd.labels, P.adj_beta[id], P.adj[id].per,
@@ -1547,6 +1694,7 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                 }
                 if (st.kind == 2) absorb_table(st.ad, t);
                 else if (st.kind == 3) reduce_table(st.rd, t);
+                else if (st.kind == 4) t = st.btab;
                 else continue;
                 where.push_back({&st, all.size()});
                 all.insert(all.end(), t.begin(), t.end());
@@ -1557,7 +1705,16 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
             CK(cudaMemcpy(dt, all.data(), all.size() * 4, cudaMemcpyHostToDevice));
             for (auto &w : where) {
                 if (w.first->kind == 2) w.first->ad.tab = dt + w.second;
-                else w.first->rd.tab = dt + w.second;
+                else if (w.first->kind == 3) w.first->rd.tab = dt + w.second;
+                else {
+                    BDesc &b = w.first->bd;
+                    const int32_t *base = dt + w.second;
+                    for (const int32_t **q : {&b.tag, &b.tbg, &b.tcg, &b.tam, &b.tcm, &b.tbn,
+                                              &b.tcn, &b.tak, &b.tbk})
+                        *q = base + (intptr_t)*q;
+                    w.first->btab.clear();
+                    w.first->btab.shrink_to_fit();
+                }
             }
             for (auto &w : pwhere) w.first->tl.ttab = dt + w.second;
         }
@@ -1800,6 +1957,12 @@ static void run_step(tn_model *m, Program &P, const Step &s, cudaStream_t st, in
         timed(pr, st, C_SPLITK, s.flops, s.bytes,
               [&] { launch_reduce<T>(s.rd, P.lscratch[s.lane], st); });
         nl += reduce_launches(s.rd);
+        return;
+    }
+    if (s.kind == 4) {
+        timed(pr, st, C_BGEMM, s.flops, s.bytes,
+              [&] { launch_bgemm<T>(s.bd, P.lscratch[s.lane], st); });
+        nl += bgemm_launches(s.bd);
         return;
     }
     if (s.kind == 0) {
@@ -3121,12 +3284,42 @@ tn_status tn_contract_dev(int nlabels, const int *sizes, int na, const int *labe
             return TN_OK;
         }
     }
+    int es = dtype == 0 ? 8 : 4;
+    // other sum-product contractions without a label summed inside one
+    // operand: the batched strided GEMM
+    if (semiring == 0) {
+        BDesc bd;
+        std::vector<int32_t> tab;
+        if (make_bgemm(card, la, false, 0, A, nullptr, lb, false, 0, B, nullptr, lc, false, 0, C,
+                       nullptr, 1, es, bd, tab)) {
+            int32_t *dtab = nullptr;
+            void *part = nullptr;
+            size_t pb = bgemm_scratch_bytes(bd, es);
+            CK(cudaMallocAsync(&dtab, tab.size() * 4, st));
+            CK(cudaMemcpyAsync(dtab, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice, st));
+            for (const int32_t **q : {&bd.tag, &bd.tbg, &bd.tcg, &bd.tam, &bd.tcm, &bd.tbn,
+                                      &bd.tcn, &bd.tak, &bd.tbk})
+                *q = dtab + (intptr_t)*q;
+            if (pb) CK(cudaMallocAsync(&part, pb, st));
+            if (dtype == 0) launch_bgemm<double>(bd, part, st);
+            else launch_bgemm<float>(bd, part, st);
+            cudaError_t e = cudaGetLastError();
+            // the pageable source of the table copy must outlive it
+            cudaError_t e2 = cudaStreamSynchronize(st);
+            cudaFreeAsync(dtab, st);
+            if (part) cudaFreeAsync(part, st);
+            if (e != cudaSuccess || e2 != cudaSuccess)
+                return fail(TN_E_CUDA, std::string("batched GEMM launch: ") +
+                                           cudaGetErrorString(e != cudaSuccess ? e : e2));
+            CK(cudaStreamSynchronize(st));
+            return TN_OK;
+        }
+    }
     CDesc d;
     std::string err = make_desc(card, la, false, 0, A, nullptr, lb, false, 0, B, nullptr, lc,
                                 false, C, nullptr, nullptr, 1,
                                 semiring == 1 ? argmax : nullptr, d);
     if (!err.empty()) return fail(TN_E_UNSUPPORTED, err);
-    int es = dtype == 0 ? 8 : 4;
     size_t sb = contract_scratch_bytes(d, es);
     void *scratch = nullptr;
     if (sb) CK(cudaMallocAsync(&scratch, sb, st));

@@ -25,7 +25,7 @@ EXPORTS = ["tn_load_model", "tn_load_model_arrays", "tn_free_model", "tn_set_ord
            "tn_last_device_ms", "tn_last_launch_count", "tn_last_error", "tn_contract_dev",
            "tn_profile", "tn_profile_steps", "tn_contract_dev_noalloc",
            "tn_reassociate", "tn_choose_slices", "tn_joint_mar"]
-PROFILE_CLASSES = ["small", "absorb", "reduce", "tcgemm", "simtgemm", "prep", "generic", "unused7"]
+PROFILE_CLASSES = ["small", "absorb", "reduce", "tcgemm", "simtgemm", "prep", "generic", "bgemm"]
 
 
 class TNError(RuntimeError):
