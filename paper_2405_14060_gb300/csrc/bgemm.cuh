@@ -33,12 +33,13 @@ struct BDesc {
     unsigned long long *mxc;       // per-item maximum of C
     int nsplit;                    // K split over this many blocks (partials in scratch)
     int64_t kchunk;                // summed indices per split (a multiple of the K tile)
-    int tile;                      // tile shape id (see bgemm.cu)
+    int tile;                      // tile shape id (see bgemm.cu); -1: does not fit
 };
 
 // Scratch bytes of the split-K partials (0 when the K space is not split).
 size_t bgemm_scratch_bytes(const BDesc &d, int elem_bytes);
-// Choose the tile shape and the K split of a descriptor (host).
+// Choose the tile shape and the K split of a descriptor (host); sets tile to
+// -1 when the contraction exceeds the kernels' index ranges.
 void bgemm_configure(BDesc &d, int elem_bytes);
 template <typename T>
 void launch_bgemm(const BDesc &d, void *scratch, cudaStream_t st);

@@ -963,7 +963,7 @@ static bool make_bgemm(const std::vector<int> &card, const Labels &lx, bool bx, 
     d.mxb_bs = by ? 1 : 0;
     d.mxc = mxo;
     bgemm_configure(d, esz);
-    return true;
+    return d.tile >= 0;
 }
 
 static bool to_micro(const CDesc &d, const char *arena, int esz, const unsigned long long *mxb,

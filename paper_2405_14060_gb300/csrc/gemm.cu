@@ -98,58 +98,140 @@ __device__ __forceinline__ void store_conv(void *out, int64_t i, TI x) {
     else ((__nv_bfloat16 *)out)[i] = __float2bfloat16_rn((float)x);
 }
 
+// Tiled form: each block walks a contiguous range of tiles (up to PT_MAXN
+// entries each, input and output runs of at least 32 entries) with two
+// shared-memory buffers: the asynchronous copies of the next tile's input are
+// in flight while the current tile is written out.  One thread advances the
+// tile's base offsets digit by digit and publishes them in shared memory.
+// Loads follow the input order (t.vin inputs per 16-byte copy when the plan
+// allows), stores the output order (t.vec outputs per 16-byte store).
+// Shared slots: input-order entry e sits at e + 4 (e / 32), which keeps
+// 16-byte groups aligned and spreads column reads over the banks.
 template <typename TI, int OT>
 __global__ void __launch_bounds__(256) k_permute_tiled(const __grid_constant__ PDesc p,
                                                        int64_t per_item) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    TI *sm = (TI *)smraw;
+    __shared__ int64_t sbase[3][3];   // per tile (mod 3): input base, output base, item
     const PTile &t = p.tl;
-    const int64_t item = blockIdx.y;
     const int n = t.tn;
+    const int nbuf = n + 4 * (n >> 5) + 4;
+    TI *sm0 = (TI *)smraw;
+    const int64_t item = blockIdx.y;
     const int32_t *tin = t.ttab, *tout = t.ttab + n, *slot = t.ttab + 2 * n;
     const TI *in = (const TI *)p.in;
     TI mxv = 0;
-    for (int64_t q = blockIdx.x; q < per_item; q += gridDim.x) {
-        int64_t bi = 0, bo = 0, beta = 0;
-        {
-            // tile counts stay below 2^31 (checked on the host): 32-bit digits
-            uint32_t g = (uint32_t)(item * per_item + q);
-            for (int k = t.nrest - 1; k >= 0; --k) {
-                uint32_t dg;
-                if (t.rsh[k] >= 0) {
-                    dg = g & (uint32_t)(t.rsz[k] - 1);
-                    g >>= t.rsh[k];
-                } else {
-                    dg = g % (uint32_t)t.rsz[k];
-                    g /= (uint32_t)t.rsz[k];
-                }
-                bi += (int64_t)dg * t.rin[k];
-                bo += (int64_t)dg * t.rout[k];
-                if (k == t.rest_beta) beta = dg;
+    // this block's tiles [q0, q1)
+    const int64_t q0 = per_item * blockIdx.x / gridDim.x;
+    const int64_t q1 = per_item * (blockIdx.x + 1) / gridDim.x;
+    // digits of the current tile (thread 0 only)
+    int32_t dg[MAXD];
+    int64_t cbi = 0, cbo = 0;
+    if (threadIdx.x == 0) {
+        uint32_t g = (uint32_t)(item * per_item + q0);
+        for (int k = t.nrest - 1; k >= 0; --k) {
+            uint32_t v;
+            if (t.rsh[k] >= 0) {
+                v = g & (uint32_t)(t.rsz[k] - 1);
+                g >>= t.rsh[k];
+            } else {
+                v = g % (uint32_t)t.rsz[k];
+                g /= (uint32_t)t.rsz[k];
             }
+            dg[k] = (int32_t)v;
+            cbi += (int64_t)v * t.rin[k];
+            cbo += (int64_t)v * t.rout[k];
         }
-        for (int e0 = threadIdx.x; e0 < n; e0 += 1024) {
-            TI v[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                int e = e0 + u * 256;
-                v[u] = e < n ? in[bi + __ldg(tin + e)] : TI(0);
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                int e = e0 + u * 256;
-                if (e < n) sm[e + (e >> 5)] = v[u];
-            }
-        }
-        __syncthreads();
-        const TI sc = p.mxi ? pow2neg<TI>(exp_of_bits(p.mxi[beta * p.mxi_bs])) : TI(1);
-        for (int e = threadIdx.x; e < n; e += 256) {
-            TI x = sm[__ldg(slot + e)] * sc;
-            store_conv<TI, OT>(p.out, bo + __ldg(tout + e), x);
-            mxv = mxv > x ? mxv : x;
-        }
-        __syncthreads();
     }
+    // thread 0: publish the bases of tile q (q0, q0 + 1, ... in order)
+    auto publish = [&](int64_t q) {
+        if (threadIdx.x != 0 || q >= q1) return;
+        if (q > q0) {
+            for (int k = t.nrest - 1; k >= 0; --k) {
+                cbi += t.rin[k];
+                cbo += t.rout[k];
+                if (++dg[k] < t.rsz[k]) break;
+                cbi -= t.rin[k] * t.rsz[k];
+                cbo -= t.rout[k] * t.rsz[k];
+                dg[k] = 0;
+            }
+        }
+        const int s = (int)(q % 3);
+        sbase[s][0] = cbi;
+        sbase[s][1] = cbo;
+        sbase[s][2] = t.rest_beta >= 0 ? dg[t.rest_beta] : 0;
+    };
+    const bool vin = t.vin > 0 && ((uintptr_t)p.in & 15) == 0;
+    auto issue = [&](int64_t q, int buf) {
+        if (q < q1) {
+            const int64_t bi = sbase[q % 3][0];
+            const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(sm0 + buf * nbuf);
+            if (vin) {
+                constexpr int GI = 16 / (int)sizeof(TI);
+                for (int e = threadIdx.x * GI; e < n; e += 256 * GI)
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                                     s0 + (uint32_t)((e + 4 * (e >> 5)) * sizeof(TI))),
+                                 "l"(in + bi + __ldg(tin + e))
+                                 : "memory");
+            } else {
+                for (int e = threadIdx.x; e < n; e += 256)
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(
+                                     s0 + (uint32_t)((e + 4 * (e >> 5)) * sizeof(TI))),
+                                 "l"(in + bi + __ldg(tin + e)), "n"(sizeof(TI))
+                                 : "memory");
+            }
+        }
+        cp_async_commit();
+    };
+    const bool vec = t.vec > 0 && ((uintptr_t)p.out & 15) == 0;
+    publish(q0);
+    __syncthreads();
+    issue(q0, 0);
+    int buf = 0;
+    for (int64_t q = q0; q < q1; ++q) {
+        publish(q + 1);
+        __syncthreads();          // bases of q + 1 visible; buffer buf ^ 1 free
+        issue(q + 1, buf ^ 1);
+        cp_async_wait<1>();
+        __syncthreads();          // tile q landed
+        const int64_t bo = sbase[q % 3][1], beta = sbase[q % 3][2];
+        const TI sc = p.mxi ? pow2neg<TI>(exp_of_bits(p.mxi[beta * p.mxi_bs])) : TI(1);
+        const TI *sm = sm0 + buf * nbuf;
+        if (vec) {
+            constexpr int G = OT == E_F64 ? 2 : OT == E_F32 ? 4 : 8;
+            for (int e0 = threadIdx.x * G; e0 < n; e0 += 256 * G) {
+                TI x[G];
+#pragma unroll
+                for (int j = 0; j < G; ++j) {
+                    x[j] = sm[__ldg(slot + e0 + j)] * sc;
+                    mxv = mxv > x[j] ? mxv : x[j];
+                }
+                const int64_t o = bo + __ldg(tout + e0);
+                if (OT == E_BF16) {
+                    uint4 v;
+                    uint32_t *w = (uint32_t *)&v;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        __nv_bfloat162 h = __floats2bfloat162_rn((float)x[2 * j], (float)x[2 * j + 1]);
+                        w[j] = *(uint32_t *)&h;
+                    }
+                    *(uint4 *)((__nv_bfloat16 *)p.out + o) = v;
+                } else if (OT == E_F32) {
+                    *(float4 *)((float *)p.out + o) =
+                        make_float4((float)x[0], (float)x[1], (float)x[2], (float)x[3]);
+                } else {
+                    *(double2 *)((double *)p.out + o) = make_double2((double)x[0], (double)x[1]);
+                }
+            }
+        } else {
+            for (int e = threadIdx.x; e < n; e += 256) {
+                TI x = sm[__ldg(slot + e)] * sc;
+                store_conv<TI, OT>(p.out, bo + __ldg(tout + e), x);
+                mxv = mxv > x ? mxv : x;
+            }
+        }
+        buf ^= 1;
+    }
+    cp_async_wait<0>();
     if (p.mxo) block_max_atomic(p.mxo + item, (double)mxv);
 }
 
@@ -245,7 +327,7 @@ void plan_permute_tiles(PDesc &p, std::vector<int32_t> &tab) {
             return;
         }
         tab[n + e] = (int32_t)off;
-        tab[2 * n + e] = (int32_t)(ein + (ein >> 5));
+        tab[2 * n + e] = (int32_t)(ein + 4 * (ein >> 5));
     }
     PTile &t = p.tl;
     t.nrest = 0;
@@ -272,6 +354,33 @@ void plan_permute_tiles(PDesc &p, std::vector<int32_t> &tab) {
     }
     t.tn = (int)n;
     t.ttab = nullptr;   // device copy of `tab`, set by the caller
+    // 16-byte stores: every aligned group of G output-ordered entries is
+    // contiguous and starts on a multiple of G elements in every tile
+    t.vec = 0;
+    {
+        const int G = p.out_type == E_F64 ? 2 : p.out_type == E_F32 ? 4 : 8;
+        bool ok = n % G == 0;
+        for (int64_t e0 = 0; ok && e0 < n; e0 += G) {
+            const int32_t o = tab[n + e0];
+            ok = o % G == 0;
+            for (int j = 1; ok && j < G; ++j) ok = tab[n + e0 + j] == o + j;
+        }
+        for (int k = 0; ok && k < t.nrest; ++k) ok = t.rout[k] % G == 0;
+        if (ok) t.vec = G;
+    }
+    // 16-byte input copies: the same condition on the input-ordered entries
+    t.vin = 0;
+    {
+        const int G = p.in_type == E_F64 ? 2 : 4;
+        bool ok = n % G == 0;
+        for (int64_t e0 = 0; ok && e0 < n; e0 += G) {
+            const int32_t o = tab[e0];
+            ok = o % G == 0;
+            for (int j = 1; ok && j < G; ++j) ok = tab[e0 + j] == o + j;
+        }
+        for (int k = 0; ok && k < t.nrest; ++k) ok = t.rin[k] % G == 0;
+        if (ok) t.vin = G;
+    }
 }
 
 void launch_permute(const PDesc &p, cudaStream_t st) {
@@ -279,9 +388,20 @@ void launch_permute(const PDesc &p, cudaStream_t st) {
     if (p.tl.tn > 0 && p.tl.ttab) {
         int nitems = (p.mxo && p.tl.rest_beta == 0) ? p.tl.rsz[0] : 1;
         int64_t per = p.tl.ntiles / nitems;
-        int64_t cap = std::max<int64_t>(1, (152LL * 8) / nitems);
+        int64_t cap = std::max<int64_t>(1, (152LL * 6) / nitems);
         dim3 grid((unsigned)std::max<int64_t>(1, std::min(per, cap)), (unsigned)nitems, 1);
-        size_t sm = (size_t)(p.tl.tn + p.tl.tn / 32 + 1) * (p.in_type == E_F64 ? 8 : 4);
+        // two tile buffers
+        size_t sm = 2 * (size_t)(p.tl.tn + 4 * (p.tl.tn / 32) + 4) * (p.in_type == E_F64 ? 8 : 4);
+        static std::once_flag once;
+        std::call_once(once, [] {
+            const int mx = 2 * (PT_MAXN + 4 * (PT_MAXN / 32) + 4) * 8;
+            cudaFuncSetAttribute(k_permute_tiled<double, E_F64>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+            cudaFuncSetAttribute(k_permute_tiled<float, E_F32>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+            cudaFuncSetAttribute(k_permute_tiled<float, E_BF16>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        });
         if (p.in_type == E_F64) k_permute_tiled<double, E_F64><<<grid, 256, sm, st>>>(p, per);
         else if (p.out_type == E_F32) k_permute_tiled<float, E_F32><<<grid, 256, sm, st>>>(p, per);
         else k_permute_tiled<float, E_BF16><<<grid, 256, sm, st>>>(p, per);

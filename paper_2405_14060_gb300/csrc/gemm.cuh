@@ -33,6 +33,8 @@ struct PTile {
     int32_t rsz[MAXD], rsh[MAXD];    // rest sizes, log2 (-1: not a power of two)
     int64_t rin[MAXD], rout[MAXD];
     int64_t ntiles;
+    int vec;                         // outputs per 16-byte store (0: one at a time)
+    int vin;                         // inputs per 16-byte copy (0: one at a time)
     const int32_t *ttab;
 };
 
