@@ -16,7 +16,10 @@
 //   k_simt_gemm  CUDA-core tiled GEMM for FP32 and FP64.
 //
 // Every mbarrier wait is bounded in time: a wait that exceeds ~2 s sets the
-// error flag and the CTA skips the rest of its work, frees its TMEM and exits.
+// error flag and the CTA skips the rest of its work.  Before it frees its
+// TMEM and exits it waits (bounded again) for the asynchronous work it has
+// already started: the TMA transfers of the last stages it issued and, via a
+// final commit, every MMA it issued.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -24,6 +27,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <mutex>
 #include <vector>
 
@@ -432,6 +436,7 @@ struct TCParams {
     unsigned long long *mxd;
     int64_t beta_div_batch, beta_div_row;
     int *err;
+    unsigned long long wait_ns;   // limit of the producer's and the MMA issuer's waits
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -452,12 +457,28 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// bounded wait: false (and the error flag set) after ~2 s
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err) {
+// bounded wait: false (and the error flag set) after `limit` ns, or at once
+// when another thread has already given up
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err,
+                                          unsigned long long limit) {
     if (mbar_try(bar, parity)) return true;
     unsigned long long t0 = gtimer();
     while (!mbar_try(bar, parity)) {
         if (*(volatile int *)err) return false;
+        if (gtimer() - t0 > limit) {
+            atomicExch(err, 1);
+            return false;
+        }
+    }
+    return true;
+}
+// wait for asynchronous work that completes on its own (TMA transfers and
+// MMAs already issued) before the CTA releases its shared memory and TMEM;
+// bounded by TC_WAIT_NS, regardless of the error flag
+__device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity, int *err) {
+    if (mbar_try(bar, parity)) return true;
+    unsigned long long t0 = gtimer();
+    while (!mbar_try(bar, parity)) {
         if (gtimer() - t0 > TC_WAIT_NS) {
             atomicExch(err, 1);
             return false;
@@ -525,9 +546,12 @@ __global__ void __launch_bounds__(128, 1)
     const int KT = p.kt;
     if (warp == 0 && lane == 0) {
         // TMA producer
+        int issued = 0;
         for (int kt = 0; kt < KT; ++kt) {
             int s = kt % TC_STAGES, round = kt / TC_STAGES;
-            if (kt >= TC_STAGES && !mbar_wait(empty0 + 8 * s, (round - 1) & 1, p.err)) break;
+            if (kt >= TC_STAGES && !mbar_wait(empty0 + 8 * s, (round - 1) & 1, p.err, p.wait_ns))
+                break;
+            issued = kt + 1;
             uint32_t fb = full0 + 8 * s;
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
                          "r"(TC_XBYTES + TC_YBYTES)
@@ -544,6 +568,11 @@ __global__ void __launch_bounds__(128, 1)
                 "l"(&ty), "r"(fb), "r"(kx), "r"((int)n0), "r"(bz)
                 : "memory");
         }
+        // the transfers of the last stages issued land before the CTA exits
+        // (already the case when the MMA issuer consumed them; it may have
+        // given up first)
+        for (int kt = issued > TC_STAGES ? issued - TC_STAGES : 0; kt < issued; ++kt)
+            mbar_drain(full0 + 8 * (kt % TC_STAGES), (kt / TC_STAGES) & 1, p.err);
     } else if (warp == 1 && lane == 0) {
         // MMA issuer: D[128 x 256] (+)= X[128 x K] * Y[256 x K]^T, 4 MMAs of 32 bytes of K per slab
         const uint32_t idesc = (1u << 4) |                               // D: F32
@@ -554,7 +583,7 @@ __global__ void __launch_bounds__(128, 1)
         bool ok = true;
         for (int kt = 0; kt < KT; ++kt) {
             int s = kt % TC_STAGES, round = kt / TC_STAGES;
-            if (!mbar_wait(full0 + 8 * s, round & 1, p.err)) { ok = false; break; }
+            if (!mbar_wait(full0 + 8 * s, round & 1, p.err, p.wait_ns)) { ok = false; break; }
             tc_fence_after();
             uint64_t ad = sdesc_sw128(smem_u32(sX + s * TC_XBYTES));
             uint64_t bd = sdesc_sw128(smem_u32(sY + s * TC_YBYTES));
@@ -577,15 +606,17 @@ __global__ void __launch_bounds__(128, 1)
                     empty0 + 8 * s)
                 : "memory");
         }
-        if (ok)
-            asm volatile(
-                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    tfull)
-                : "memory");
+        // arrives once every MMA issued above has completed (also after a
+        // give-up, so that TMEM is released only when idle)
+        (void)ok;
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                tfull)
+            : "memory");
     }
     __syncwarp();
     // epilogue: warp w drains TMEM lanes 32w..32w+31 (rows of the tile)
-    bool have = mbar_wait(tfull, 0, p.err);
+    bool have = mbar_drain(tfull, 0, p.err) && !*(volatile int *)p.err;
     have = __all_sync(0xffffffffu, have);
     tc_fence_after();
     const int64_t row = m0 + warp * 32 + lane;
@@ -708,6 +739,10 @@ cudaError_t launch_tc_gemm(const GDesc &g, int *err_flag, cudaStream_t st) {
     p.beta_div_batch = g.beta_div_batch;
     p.beta_div_row = g.beta_div_row;
     p.err = err_flag;
+    // test hook: a shorter limit for the pipeline's waits (nanoseconds), so
+    // that tests can make them give up without any fault
+    p.wait_ns = TC_WAIT_NS;
+    if (const char *w = getenv("TN_TEST_TC_WAIT_NS")) p.wait_ns = strtoull(w, nullptr, 10);
     p.ntn = (g.C + TC_BN - 1) / TC_BN;
     p.ntm = (g.R + TC_BM - 1) / TC_BM;
     if (p.ntn * p.ntm * g.batch >= (1LL << 31)) return cudaErrorInvalidConfiguration;
