@@ -198,8 +198,14 @@ tn_status tn_pr(tn_model *m, int batch, const int32_t *evid, const tn_options *o
 
 /* MAR: logz as tn_pr, and marg[b][sum card] = p(v = x | e_b) for every
  * variable (an observed variable gets the indicator of its value).  One
- * forward and one reverse (adjoint) pass over the tree (Sec. MAR).
- * Errors: TN_E_ARG when some p(e_b) = 0. */
+ * forward and one reverse (adjoint) pass over the tree (Sec. MAR).  The
+ * reverse pass reads the forward intermediates; when keeping all of them
+ * does not fit the device memory or opts->hbm_budget_bytes even for one
+ * evidence set, the largest ones (never a parent and its child) are not
+ * kept: the reverse pass recomputes each from its kept operands just before
+ * it is read (checkpointing; the extra work shows as class 8 of tn_profile).
+ * Errors: TN_E_ARG when some p(e_b) = 0; TN_E_OOM when even that does not
+ * fit. */
 tn_status tn_mar(tn_model *m, int batch, const int32_t *evid, const tn_options *opts,
                  double *logz, double *marg);
 
@@ -272,12 +278,15 @@ int64_t tn_last_launch_count(const tn_model *m);
 
 /* Profile one PR (task 0) or PR + MAR (task 1) pass kernel by kernel (each
  * launch timed with CUDA events on the model's stream, outside any graph),
- * averaged over `reps` passes.  out[8][4] per kernel class: milliseconds,
+ * averaged over `reps` passes.  out[9][4] per kernel class: milliseconds,
  * launches, algorithmic FLOPs (2 per multiply-add of a contraction) and
  * algorithmic bytes (operands and result once).  Classes: 0 leaves and
  * finalisation (not timed, reported as 0), 1 streaming absorb, 2 streaming
  * reduction (or split-K), 3 tcgen05 GEMM, 4 CUDA-core GEMM, 5 operand
- * preparation / scatter, 6 generic strided contraction, 7 unused. */
+ * preparation / scatter, 6 generic strided contraction, 7 batched strided
+ * GEMM, 8 recomputation: forward steps that a checkpointed MAR program
+ * re-runs in its backward pass (their FLOPs and bytes are extra work, not
+ * part of the algorithmic count of the other classes). */
 tn_status tn_profile(tn_model *m, int task, int batch, const int32_t *evid,
                      const tn_options *opts, int reps, double *out);
 

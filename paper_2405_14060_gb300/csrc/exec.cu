@@ -117,7 +117,7 @@ enum Kind { K_PR = 0, K_MAR = 1, K_MAP = 2, K_SAMPLE = 3, K_SUMNET = 4, K_MAXNET
 
 // Kernel classes for profiling.
 enum Cls { C_SMALL = 0, C_STREAM = 1, C_SPLITK = 2, C_TCGEMM = 3, C_SIMTGEMM = 4, C_PREP = 5,
-           C_GENERIC = 6, C_BGEMM = 7, C_NCLS = 8 };
+           C_GENERIC = 6, C_BGEMM = 7, C_RECOMP = 8, C_NCLS = 9 };
 
 struct GemmOp {
     PDesc px, py, post;
@@ -144,6 +144,7 @@ struct Step {
     const char *why = "";          // why a strided contraction did not stream (plan trace)
     int node = -1;                 // the tensor this step writes: fwd[node] or adj[node]
     bool adjoint = false;
+    bool recompute = false;        // re-runs a dropped forward step before its use
     int lane = 0;                  // stream of the step inside the program's graph
     std::vector<int> waits;        // events (other lanes' results) to wait for first
     int rec = -1;                  // event to record after the step (-1: none)
@@ -155,6 +156,12 @@ struct Program {
     Plan plan;
     std::vector<Slot> fwd, adj;
     std::vector<char> adj_beta, need_adj;
+    // checkpointing (MAR under a memory budget): forward tensors not kept
+    // after their parent's forward step, recomputed into rec_off[] by the
+    // backward pass just before the parent's adjoint steps read them
+    std::vector<char> drop;
+    std::vector<int64_t> rec_off;
+    int ndrop = 0;
     int64_t nmx = 0;
     DevMem mem;
     char *arena = nullptr;
@@ -1248,6 +1255,16 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
             }
         }
     }
+    P.drop.assign(NN, 0);
+    P.rec_off.assign(NN, -1);
+    // is fwd[c] read by the adjoint steps of its parent?  (fwd[a] by the
+    // sibling's adjoint B-bar, fwd[b] by A-bar)
+    auto fwd_read_back = [&](int c) {
+        const int par = pl.node[c].parent;
+        if (par < 0 || !backward) return false;
+        const Node &pn = pl.node[par];
+        return P.need_adj[c == pn.a ? pn.b : pn.a] != 0;
+    };
     auto plan_arena = [&](bool recycle) {
         OffsetAlloc A;
         for (int id = 0; id < n; ++id) P.fwd[id].off = A.alloc(P.fwd[id].elems);
@@ -1259,15 +1276,24 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
             if (recycle && !keep_all && !P.micro[id]) {
                 A.release(P.fwd[nd.a].off, P.fwd[nd.a].elems);
                 A.release(P.fwd[nd.b].off, P.fwd[nd.b].elems);
+            } else if (!P.micro[id]) {
+                for (int c : {nd.a, nd.b})
+                    if (P.drop[c]) A.release(P.fwd[c].off, P.fwd[c].elems);
             }
         }
         if (backward) {
             P.adj[pl.root].off = A.alloc(P.adj[pl.root].elems);
             for (int id : bwd_order) {
                 const Node &nd = pl.node[id];
+                for (int c : {nd.a, nd.b}) {
+                    P.rec_off[c] = -1;
+                    if (P.drop[c] && fwd_read_back(c)) P.rec_off[c] = A.alloc(P.fwd[c].elems);
+                }
                 for (int c : {nd.a, nd.b})
                     if (P.need_adj[c]) P.adj[c].off = A.alloc(P.adj[c].elems);
                 if (recycle && !P.micro[id]) A.release(P.adj[id].off, P.adj[id].elems);
+                for (int c : {nd.a, nd.b})
+                    if (P.rec_off[c] >= 0) A.release(P.rec_off[c], P.fwd[c].elems);
             }
         }
         return A.top;
@@ -1282,6 +1308,42 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
     }
     P.nlanes = nl_used;
     int64_t arena_top = plan_arena(nl_used == 1);
+    int64_t budget = opts ? opts->hbm_budget_bytes : 0;
+    size_t freeb = 0, totb = 0;
+    CK(cudaMemGetInfo(&freeb, &totb));
+    // the memory the program may take: the budget, else what is free
+    const double limit = budget > 0 ? (double)budget : (double)freeb - (double)(256u << 20);
+    auto need_of = [&](int64_t top) { return (double)top * P.esz + (double)nmx * 8; };
+    if (kind == K_MAR && nbeta == 1 && need_of(arena_top) > limit) {
+        // checkpointing (a batch of evidence sets is split into smaller
+        // batches first, which costs no extra work): drop the largest forward
+        // tensors, no two of them parent and child (a recompute reads only
+        // kept tensors), until the arena fits; one lane (the arena is
+        // recycled in step order)
+        nl_used = 1;
+        P.nlanes = 1;
+        std::fill(P.lane.begin(), P.lane.end(), 0);
+        arena_top = plan_arena(true);
+        std::vector<int> cand;
+        for (int id = n; id < NN; ++id)
+            if (id != pl.root && !P.micro[id] && fwd_read_back(id)) cand.push_back(id);
+        std::stable_sort(cand.begin(), cand.end(),
+                         [&](int x, int y) { return P.fwd[x].elems > P.fwd[y].elems; });
+        for (int c : cand) {
+            if (need_of(arena_top) <= limit) break;
+            const Node &cn = pl.node[c];
+            if (P.drop[cn.a] || P.drop[cn.b] || (cn.parent >= 0 && P.drop[cn.parent])) continue;
+            P.drop[c] = 1;
+            int64_t t = plan_arena(true);
+            if (t < arena_top) {
+                arena_top = t;
+                ++P.ndrop;
+            } else {
+                P.drop[c] = 0;
+            }
+        }
+        arena_top = plan_arena(true);
+    }
     P.arena_elems = arena_top;
     // argmax buffers
     int64_t am_total = 0;
@@ -1293,9 +1355,6 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
         }
     // ---- budget and allocation
     size_t need = (size_t)P.arena_elems * P.esz + (size_t)nmx * 8 + (size_t)am_total * 4;
-    int64_t budget = opts ? opts->hbm_budget_bytes : 0;
-    size_t freeb = 0, totb = 0;
-    CK(cudaMemGetInfo(&freeb, &totb));
     if ((budget > 0 && (int64_t)need > budget) || need + (256u << 20) > freeb) {
         char buf[256];
         snprintf(buf, sizeof buf,
@@ -1365,6 +1424,11 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
     auto mxp = [&](int64_t i) { return maxplus ? nullptr : P.mx + i; };
     auto fptr = [&](int id) { return (char *)P.arena + P.fwd[id].off * P.esz; };
     auto aptr = [&](int id) { return (char *)P.arena + P.adj[id].off * P.esz; };
+    // forward tensors as the backward pass reads them (dropped ones from
+    // their recompute slots)
+    auto bfptr = [&](int id) {
+        return P.drop[id] ? (char *)P.arena + P.rec_off[id] * P.esz : fptr(id);
+    };
     const int store_t = dtype == 0 ? E_F64 : E_F32;
     size_t scratch = 0, need_x = 0, need_y = 0, need_d = 0;
     auto add_gemm = [&](std::vector<Step> &steps, const Opnd &X, const Opnd &Y, const Labels &bt,
@@ -1387,17 +1451,21 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
         return "";
     };
     auto per_items = [&](bool b) { return b ? (double)nbeta : 1.0; };
-    for (int id = n; id < NN; ++id) {
+    // the forward step of node id writing its result at `outp` (the arena
+    // slot, or the recompute slot of a dropped tensor); the operands are
+    // always read from their forward slots
+    auto fwd_step = [&](int id, char *outp, std::vector<Step> &steps, bool recomp,
+                        bool record_desc) -> tn_status {
         const Node &nd = pl.node[id];
         CDesc d;
         err = make_desc(net.card, pl.node[nd.a].labels, pl.node[nd.a].beta, P.fwd[nd.a].per,
                         fptr(nd.a), mxp(P.fwd[nd.a].mx), pl.node[nd.b].labels, pl.node[nd.b].beta,
                         P.fwd[nd.b].per, fptr(nd.b), mxp(P.fwd[nd.b].mx), nd.labels, nd.beta,
-                        fptr(id), mxp(P.fwd[id].mx), &nd.elim, nbeta,
+                        outp, mxp(P.fwd[id].mx), &nd.elim, nbeta,
                         maxplus ? P.am + P.am_off[id] : nullptr, d);
         if (!err.empty()) return fail(TN_E_UNSUPPORTED, err);
-        P.fdesc.push_back(d);
-        if (P.micro[id]) continue;
+        if (record_desc) P.fdesc.push_back(d);
+        if (P.micro[id]) return TN_OK;
         double items = per_items(nd.beta);
         double flops = 2.0 * nd.muladds * items;
         double bytes = (double)P.esz * (P.fwd[nd.a].elems + P.fwd[nd.b].elems + P.fwd[id].elems);
@@ -1406,10 +1474,11 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                    P.mx + P.fwd[nd.ga].mx};
             Opnd Y{&pl.node[nd.gb].labels, pl.node[nd.gb].beta, P.fwd[nd.gb].per, fptr(nd.gb),
                    P.mx + P.fwd[nd.gb].mx};
-            err = add_gemm(P.fsteps, X, Y, nd.gbt, nd.gm, nd.gn, nd.elim, nd.labels, nd.beta,
-                           fptr(id), P.mx + P.fwd[id].mx, flops, bytes);
+            err = add_gemm(steps, X, Y, nd.gbt, nd.gm, nd.gn, nd.elim, nd.labels, nd.beta,
+                           outp, P.mx + P.fwd[id].mx, flops, bytes);
             if (!err.empty()) return fail(TN_E_UNSUPPORTED, err);
-            P.fsteps.back().node = id;
+            steps.back().node = id;
+            steps.back().recompute = recomp;
         } else {
             Step st;
             st.semiring = maxplus ? MAXPLUS : SUM;
@@ -1419,13 +1488,13 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
             absorb_reject = "";
             if (make_absorb(net.card, na.labels, na.beta, P.fwd[nd.a].per, fptr(nd.a),
                             mxp(P.fwd[nd.a].mx), nb.labels, nb.beta, P.fwd[nd.b].per, fptr(nd.b),
-                            mxp(P.fwd[nd.b].mx), nd.labels, nd.beta, P.fwd[id].per, fptr(id),
+                            mxp(P.fwd[nd.b].mx), nd.labels, nd.beta, P.fwd[id].per, outp,
                             mxp(P.fwd[id].mx), &nd.elim, nbeta,
                             maxplus ? P.am + P.am_off[id] : nullptr, st.ad) ||
                 ((st.why = absorb_reject), false) ||
                 make_absorb(net.card, nb.labels, nb.beta, P.fwd[nd.b].per, fptr(nd.b),
                             mxp(P.fwd[nd.b].mx), na.labels, na.beta, P.fwd[nd.a].per, fptr(nd.a),
-                            mxp(P.fwd[nd.a].mx), nd.labels, nd.beta, P.fwd[id].per, fptr(id),
+                            mxp(P.fwd[nd.a].mx), nd.labels, nd.beta, P.fwd[id].per, outp,
                             mxp(P.fwd[id].mx), &nd.elim, nbeta,
                             maxplus ? P.am + P.am_off[id] : nullptr, st.ad)) {
                 st.kind = 2;
@@ -1433,7 +1502,7 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                        make_reduce(net.card, na.labels, na.beta, P.fwd[nd.a].per, fptr(nd.a),
                                    mxp(P.fwd[nd.a].mx), nb.labels, nb.beta, P.fwd[nd.b].per,
                                    fptr(nd.b), mxp(P.fwd[nd.b].mx), nd.labels, nd.beta,
-                                   P.fwd[id].per, fptr(id), mxp(P.fwd[id].mx), nbeta, st.rd) &&
+                                   P.fwd[id].per, outp, mxp(P.fwd[id].mx), nbeta, st.rd) &&
                        st.rd.nm >= 4096) {
                 st.kind = 3;
                 scratch = std::max(scratch, reduce_scratch_bytes(st.rd, P.esz));
@@ -1441,7 +1510,7 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                        make_bgemm(net.card, na.labels, na.beta, P.fwd[nd.a].per, fptr(nd.a),
                                   mxp(P.fwd[nd.a].mx), nb.labels, nb.beta, P.fwd[nd.b].per,
                                   fptr(nd.b), mxp(P.fwd[nd.b].mx), nd.labels, nd.beta,
-                                  P.fwd[id].per, fptr(id), mxp(P.fwd[id].mx), nbeta, P.esz, st.bd,
+                                  P.fwd[id].per, outp, mxp(P.fwd[id].mx), nbeta, P.esz, st.bd,
                                   st.btab)) {
                 st.kind = 4;
                 scratch = std::max(scratch, bgemm_scratch_bytes(st.bd, P.esz));
@@ -1451,8 +1520,14 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                 scratch = std::max(scratch, contract_scratch_bytes(d, P.esz));
             }
             st.node = id;
-            P.fsteps.push_back(st);
+            st.recompute = recomp;
+            steps.push_back(st);
         }
+        return TN_OK;
+    };
+    for (int id = n; id < NN; ++id) {
+        tn_status fs = fwd_step(id, fptr(id), P.fsteps, false, true);
+        if (fs) return fs;
     }
     if (backward) {
         for (int id = NN - 1; id >= n; --id) {
@@ -1460,13 +1535,18 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
             const Node &nd = pl.node[id];
             const Node &na = pl.node[nd.a], &nb = pl.node[nd.b];
             char *cbar = aptr(id);
+            for (int c : {nd.a, nd.b})
+                if (P.drop[c] && P.rec_off[c] >= 0) {
+                    tn_status rs = fwd_step(c, bfptr(c), P.bsteps, true, false);
+                    if (rs) return rs;
+                }
             double items = per_items(P.adj_beta[id]);
             double flops = 2.0 * nd.muladds * items;
             if (nd.gemm) {
                 const Node &xa = pl.node[nd.ga], &xb = pl.node[nd.gb];
                 Opnd Cb{&nd.labels, (bool)P.adj_beta[id], P.adj[id].per, cbar, P.mx + P.adj[id].mx};
-                Opnd A{&xa.labels, xa.beta, P.fwd[nd.ga].per, fptr(nd.ga), P.mx + P.fwd[nd.ga].mx};
-                Opnd Bo{&xb.labels, xb.beta, P.fwd[nd.gb].per, fptr(nd.gb), P.mx + P.fwd[nd.gb].mx};
+                Opnd A{&xa.labels, xa.beta, P.fwd[nd.ga].per, bfptr(nd.ga), P.mx + P.fwd[nd.ga].mx};
+                Opnd Bo{&xb.labels, xb.beta, P.fwd[nd.gb].per, bfptr(nd.gb), P.mx + P.fwd[nd.gb].mx};
                 if (P.need_adj[nd.ga]) {
                     // Abar[bt, m, k] = sum_n Cbar[bt, m, n] B[bt, k, n]
                     double bytes = (double)P.esz * (P.adj[id].elems + P.fwd[nd.gb].elems +
@@ -1498,10 +1578,10 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                 st.bytes = (double)P.esz * (P.adj[id].elems + P.fwd[nd.b].elems + P.adj[nd.a].elems);
                 if (make_absorb(net.card, nd.labels, P.adj_beta[id], P.adj[id].per, cbar,
                                 P.mx + P.adj[id].mx, nb.labels, nb.beta, P.fwd[nd.b].per,
-                                fptr(nd.b), P.mx + P.fwd[nd.b].mx, na.labels, P.adj_beta[nd.a],
+                                bfptr(nd.b), P.mx + P.fwd[nd.b].mx, na.labels, P.adj_beta[nd.a],
                                 P.adj[nd.a].per, aptr(nd.a), P.mx + P.adj[nd.a].mx, nullptr, nbeta,
                                 nullptr, st.ad) ||
-                    make_absorb(net.card, nb.labels, nb.beta, P.fwd[nd.b].per, fptr(nd.b),
+                    make_absorb(net.card, nb.labels, nb.beta, P.fwd[nd.b].per, bfptr(nd.b),
                                 P.mx + P.fwd[nd.b].mx, nd.labels, P.adj_beta[id], P.adj[id].per,
                                 cbar, P.mx + P.adj[id].mx, na.labels, P.adj_beta[nd.a],
                                 P.adj[nd.a].per, aptr(nd.a), P.mx + P.adj[nd.a].mx, nullptr, nbeta,
@@ -1509,7 +1589,7 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                     st.kind = 2;
                 } else if (make_bgemm(net.card, nd.labels, P.adj_beta[id], P.adj[id].per, cbar,
                                       P.mx + P.adj[id].mx, nb.labels, nb.beta, P.fwd[nd.b].per,
-                                      fptr(nd.b), P.mx + P.fwd[nd.b].mx, na.labels,
+                                      bfptr(nd.b), P.mx + P.fwd[nd.b].mx, na.labels,
                                       P.adj_beta[nd.a], P.adj[nd.a].per, aptr(nd.a),
                                       P.mx + P.adj[nd.a].mx, nbeta, P.esz, st.bd, st.btab)) {
                     st.kind = 4;
@@ -1517,7 +1597,7 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                 } else {
                     err = make_desc(net.card, nd.labels, P.adj_beta[id], P.adj[id].per, cbar,
                                     P.mx + P.adj[id].mx, nb.labels, nb.beta, P.fwd[nd.b].per,
-                                    fptr(nd.b), P.mx + P.fwd[nd.b].mx, na.labels, P.adj_beta[nd.a],
+                                    bfptr(nd.b), P.mx + P.fwd[nd.b].mx, na.labels, P.adj_beta[nd.a],
                                     aptr(nd.a), P.mx + P.adj[nd.a].mx, nullptr, nbeta, nullptr,
                                     st.d);
                     if (!err.empty()) return fail(TN_E_UNSUPPORTED, err);
@@ -1535,25 +1615,25 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                 st.flops = flops;
                 st.bytes = (double)P.esz * (P.fwd[nd.a].elems + P.adj[id].elems + P.adj[nd.b].elems);
                 if (P.adj[nd.b].elems >= (1 << 16) &&
-                    (make_absorb(net.card, na.labels, na.beta, P.fwd[nd.a].per, fptr(nd.a),
+                    (make_absorb(net.card, na.labels, na.beta, P.fwd[nd.a].per, bfptr(nd.a),
                                  P.mx + P.fwd[nd.a].mx, nd.labels, P.adj_beta[id], P.adj[id].per,
                                  cbar, P.mx + P.adj[id].mx, nb.labels, P.adj_beta[nd.b],
                                  P.adj[nd.b].per, aptr(nd.b), P.mx + P.adj[nd.b].mx, nullptr,
                                  nbeta, nullptr, st.ad) ||
                      make_absorb(net.card, nd.labels, P.adj_beta[id], P.adj[id].per, cbar,
                                  P.mx + P.adj[id].mx, na.labels, na.beta, P.fwd[nd.a].per,
-                                 fptr(nd.a), P.mx + P.fwd[nd.a].mx, nb.labels, P.adj_beta[nd.b],
+                                 bfptr(nd.a), P.mx + P.fwd[nd.a].mx, nb.labels, P.adj_beta[nd.b],
                                  P.adj[nd.b].per, aptr(nd.b), P.mx + P.adj[nd.b].mx, nullptr,
                                  nbeta, nullptr, st.ad))) {
                     st.kind = 2;
-                } else if (make_reduce(net.card, na.labels, na.beta, P.fwd[nd.a].per, fptr(nd.a),
+                } else if (make_reduce(net.card, na.labels, na.beta, P.fwd[nd.a].per, bfptr(nd.a),
                                 P.mx + P.fwd[nd.a].mx, nd.labels, P.adj_beta[id], P.adj[id].per,
                                 cbar, P.mx + P.adj[id].mx, nb.labels, P.adj_beta[nd.b],
                                 P.adj[nd.b].per, aptr(nd.b), P.mx + P.adj[nd.b].mx, nbeta, st.rd) &&
                     st.rd.nm >= 4096) {
                     st.kind = 3;
                     scratch = std::max(scratch, reduce_scratch_bytes(st.rd, P.esz));
-                } else if (make_bgemm(net.card, na.labels, na.beta, P.fwd[nd.a].per, fptr(nd.a),
+                } else if (make_bgemm(net.card, na.labels, na.beta, P.fwd[nd.a].per, bfptr(nd.a),
                                       P.mx + P.fwd[nd.a].mx, nd.labels, P.adj_beta[id],
                                       P.adj[id].per, cbar, P.mx + P.adj[id].mx, nb.labels,
                                       P.adj_beta[nd.b], P.adj[nd.b].per, aptr(nd.b),
@@ -1561,7 +1641,7 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                     st.kind = 4;
                     scratch = std::max(scratch, bgemm_scratch_bytes(st.bd, P.esz));
                 } else {
-                    err = make_desc(net.card, na.labels, na.beta, P.fwd[nd.a].per, fptr(nd.a),
+                    err = make_desc(net.card, na.labels, na.beta, P.fwd[nd.a].per, bfptr(nd.a),
                                     P.mx + P.fwd[nd.a].mx, nd.labels, P.adj_beta[id], P.adj[id].per,
                                     cbar, P.mx + P.adj[id].mx, nb.labels, P.adj_beta[nd.b],
                                     aptr(nd.b), P.mx + P.adj[nd.b].mx, nullptr, nbeta, nullptr,
@@ -1948,44 +2028,46 @@ static void timed(Prof *pr, cudaStream_t st, int cls, double flops, double bytes
 
 template <typename T>
 static void run_step(tn_model *m, Program &P, const Step &s, cudaStream_t st, int &nl, Prof *pr) {
+    // recompute steps are profiled as their own class (not algorithmic work)
+    auto cls = [&](int c) { return s.recompute ? (int)C_RECOMP : c; };
     if (s.kind == 2) {
-        timed(pr, st, C_STREAM, s.flops, s.bytes, [&] { launch_absorb<T>(s.ad, s.semiring, st); });
+        timed(pr, st, cls(C_STREAM), s.flops, s.bytes, [&] { launch_absorb<T>(s.ad, s.semiring, st); });
         ++nl;
         return;
     }
     if (s.kind == 3) {
-        timed(pr, st, C_SPLITK, s.flops, s.bytes,
+        timed(pr, st, cls(C_SPLITK), s.flops, s.bytes,
               [&] { launch_reduce<T>(s.rd, P.lscratch[s.lane], st); });
         nl += reduce_launches(s.rd);
         return;
     }
     if (s.kind == 4) {
-        timed(pr, st, C_BGEMM, s.flops, s.bytes,
+        timed(pr, st, cls(C_BGEMM), s.flops, s.bytes,
               [&] { launch_bgemm<T>(s.bd, P.lscratch[s.lane], st); });
         nl += bgemm_launches(s.bd);
         return;
     }
     if (s.kind == 0) {
-        int cls = contract_uses_splitk(s.d) ? C_SPLITK : C_GENERIC;
-        timed(pr, st, cls, s.flops, s.bytes, [&] {
+        int c = cls(contract_uses_splitk(s.d) ? C_SPLITK : C_GENERIC);
+        timed(pr, st, c, s.flops, s.bytes, [&] {
             launch_contract<T>(s.d, s.semiring, P.lscratch[s.lane], P.scratch_bytes, st, &nl);
         });
         return;
     }
     const GemmOp &g = s.g;
-    timed(pr, st, C_PREP, 0, g.prep_bytes, [&] {
+    timed(pr, st, cls(C_PREP), 0, g.prep_bytes, [&] {
         if (!g.x_in_place) launch_permute(g.px, st);
         launch_permute(g.py, st);
     });
     nl += g.x_in_place ? 1 : 2;
     if (g.tc) {
-        timed(pr, st, C_TCGEMM, s.flops, s.bytes, [&] { launch_tc_gemm(g.g, m->d_err, st); });
+        timed(pr, st, cls(C_TCGEMM), s.flops, s.bytes, [&] { launch_tc_gemm(g.g, m->d_err, st); });
     } else {
-        timed(pr, st, C_SIMTGEMM, s.flops, s.bytes, [&] { launch_simt_gemm(g.g, st); });
+        timed(pr, st, cls(C_SIMTGEMM), s.flops, s.bytes, [&] { launch_simt_gemm(g.g, st); });
     }
     ++nl;
     if (g.has_post) {
-        timed(pr, st, C_PREP, 0, g.post_bytes, [&] { launch_permute(g.post, st); });
+        timed(pr, st, cls(C_PREP), 0, g.post_bytes, [&] { launch_permute(g.post, st); });
         ++nl;
     }
 }
@@ -3346,7 +3428,7 @@ tn_status tn_profile(tn_model *m, int task, int batch, const int32_t *evid,
 
 tn_status tn_profile_steps(tn_model *m, int task, int batch, const int32_t *evid,
                            const tn_options *opts, int cap, double *steps, int *nsteps) {
-    double cls[32];
+    double cls[4 * C_NCLS];
     return profile_impl(m, task, batch, evid, opts, 1, cls, cap, steps, nsteps);
 }
 

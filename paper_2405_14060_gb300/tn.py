@@ -25,7 +25,8 @@ EXPORTS = ["tn_load_model", "tn_load_model_arrays", "tn_free_model", "tn_set_ord
            "tn_last_device_ms", "tn_last_launch_count", "tn_last_error", "tn_contract_dev",
            "tn_profile", "tn_profile_steps", "tn_contract_dev_noalloc",
            "tn_reassociate", "tn_choose_slices", "tn_joint_mar"]
-PROFILE_CLASSES = ["small", "absorb", "reduce", "tcgemm", "simtgemm", "prep", "generic", "bgemm"]
+PROFILE_CLASSES = ["small", "absorb", "reduce", "tcgemm", "simtgemm", "prep", "generic", "bgemm",
+                   "recompute"]
 
 
 class TNError(RuntimeError):
@@ -308,12 +309,12 @@ class Model:
                              1 if tables_are_log else 0, ctypes.byref(o), logz.data_ptr(),
                              marg.data_ptr(), None if grad is None else grad.data_ptr()))
 
-    def profile(self, task="mar", evid=None, batch=1, prec="tf32", reps=3):
+    def profile(self, task="mar", evid=None, batch=1, prec="tf32", reps=3, budget=0):
         """Per kernel class: ms, launches, FLOPs, bytes of one pass (averaged)."""
         e = None if evid is None else np.ascontiguousarray(evid, np.int32).reshape(-1, self.nvars)
         b = batch if e is None else e.shape[0]
-        out = np.zeros(32)
-        o = _opts(prec)
+        out = np.zeros(4 * len(PROFILE_CLASSES))
+        o = _opts(prec, budget)
         _ck(lib().tn_profile(self._h, 0 if task == "pr" else 1, b,
                              None if e is None else _ptr(e), ctypes.byref(o), reps, _ptr(out)))
         res = {}

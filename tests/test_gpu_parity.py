@@ -517,6 +517,62 @@ def test_sub_batching_under_budget():
     np.testing.assert_allclose(lzp, ref_lz, rtol=1e-4)
 
 
+def test_mar_checkpointing_under_budget():
+    """MAR under a memory budget below its forward cache (Sec. MAR: the
+    reverse pass reads the forward intermediates): the largest ones are not
+    kept and the reverse pass recomputes them.  At the smallest budget that
+    runs (bisected to 1/256), FP64 marginals and log Z equal the unlimited
+    run and the oracle within 1e-10, and the profile shows the recomputation
+    as its own class (recomputation is chosen only when keeping every
+    forward tensor does not fit)."""
+    m = synth.grid_ising(16, 19)
+    lz_ref, marg_ref = oracle.ve_mar(m)
+    M = tn.Model.from_synth(m)
+    tree = M.optimize_order(0)
+    M.set_order(*tree)
+    lz0, mg0 = M.mar(prec="fp64")
+
+    def fresh():
+        X = tn.Model.from_synth(m)
+        X.set_order(*tree)
+        return X
+
+    def runs(b):
+        try:
+            fresh().mar(prec="fp64", budget=b)
+            return True
+        except tn.TNError as e:
+            assert e.status == 4, e
+            return False
+
+    def smallest_budget():
+        hi = 1 << 16
+        while not runs(hi):
+            hi *= 2
+        lo = hi // 2
+        while hi - lo > max(4096, hi // 256):
+            mid = (lo + hi) // 2
+            if runs(mid):
+                hi = mid
+            else:
+                lo = mid
+        return hi, fresh()
+    b, X = smallest_budget()
+    lz, mg = X.mar(prec="fp64", budget=b)
+    assert abs(lz[0] - lz0[0]) < 1e-12 and abs(lz[0] - lz_ref) < 1e-10
+    np.testing.assert_allclose(mg, mg0, rtol=0, atol=1e-12)
+    _marg_close(X, mg[0], marg_ref, 1e-10)
+    prof = fresh().profile("mar", prec="fp64", reps=1, budget=b)
+    assert prof.get("recompute", {}).get("launches", 0) > 0, prof
+    # without recomputation the same tree needs more memory: the unlimited
+    # program's profile has no recompute class, and at budget b the FP32
+    # program (half the bytes) needs fewer recomputations or none
+    assert "recompute" not in fresh().profile("mar", prec="fp64", reps=1)
+    lz32, mg32 = fresh().mar(prec="fp32", budget=b)
+    assert abs(lz32[0] - lz_ref) <= 1e-4 * abs(lz_ref)
+    assert np.max(np.abs(mg32 - mg0)) < 1e-3
+
+
 def test_workload4_batched_slice():
     """Workload 4 (3-regular, 200 spins, evidence sets with 10% observed) on
     its annealed tree: a batch of 16 evidence sets in BF16 and FP64 against
