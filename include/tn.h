@@ -72,7 +72,9 @@ typedef struct {
     tn_prec prec;               /* default TN_FP64 */
     int64_t hbm_budget_bytes;   /* 0 = no limit beyond the device's memory */
     int max_slices;             /* reserved (slicing is set by tn_set_order) */
-    int autotune;               /* reserved (tile shapes are fixed per kernel family) */
+    int autotune;               /* 1: on a program's first use, time a few launch shapes
+                                   (graph lanes, streaming-kernel blocks per SM) and
+                                   keep the fastest (cached per model and program) */
     void *cuda_stream;          /* cudaStream_t for the _dev variants; NULL = default */
 } tn_options;                   /* a NULL options pointer means all defaults */
 
@@ -268,6 +270,18 @@ tn_status tn_pr_dev(tn_model *m, int batch, const int32_t *evid,
 tn_status tn_mar_dev(tn_model *m, int batch, const int32_t *evid,
                      const double *factor_tables, int tables_are_log,
                      const tn_options *opts, double *logz, double *marg, double *grad);
+
+/* Facts about the program that tn_pr (task 0) or tn_mar (task 1) runs for
+ * `batch` evidence sets with these options (it is built, autotuned when
+ * opts->autotune is set, and cached, as a task call would).  out[8]:
+ *   0 bytes of its tensor arena, 1 bytes that arena takes when every forward
+ *   tensor is kept, 2 forward tensors the MAR reverse pass recomputes
+ *   (checkpointing), 3 kernel launches per pass, 4 streams (lanes) of its
+ *   captured graph, 5 blocks per SM of the streaming absorb kernels (0: the
+ *   default), 6 1 if the launch shapes were chosen by the autotuner, 7 the
+ *   evidence sets per pass (the sub-batch that fits the memory). */
+tn_status tn_program_stats(tn_model *m, int task, int batch, const tn_options *opts,
+                           double *out);
 
 /* Device-side duration of the last task's kernels in milliseconds
  * (CUDA events around the launch on the task's stream). */

@@ -150,8 +150,18 @@ struct Step {
     int rec = -1;                  // event to record after the step (-1: none)
 };
 
+// Launch-shape choices of a program: fixed defaults, or the fastest of a
+// few candidates timed by the autotuner on the program's first use.
+struct Tune {
+    int max_lanes = 4;     // streams of the captured graph (1: every step in order)
+    int absorb_bps = 0;    // blocks per SM of the streaming absorb kernels (0: default)
+    bool tuned = false;
+};
+
 struct Program {
     int kind = 0, dtype = 0, esz = 8, nbeta = 1;
+    Tune tune;
+    int64_t keep_all_elems = 0;    // arena entries when every forward tensor is kept
     bool grads = false;
     Plan plan;
     std::vector<Slot> fwd, adj;
@@ -245,6 +255,7 @@ struct tn_model {
     std::vector<cudaStream_t> lanes;   // extra streams that graph capture forks onto
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::map<std::tuple<int, int, int, int>, std::unique_ptr<Program>> progs;
+    std::map<std::tuple<int, int, int, int>, Tune> tuned;   // autotuner choices per program key
     std::unique_ptr<MmapCache> mmap;
     double last_ms = 0;
     int64_t last_launches = 0;
@@ -1128,7 +1139,9 @@ static void trace_program(const Program &P) {
 // Build (plan, allocate, describe, capture) a program.
 tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind, int dtype,
                         int nbeta, bool grads, const tn_options *opts, Program &P,
-                        const std::vector<LeafRec> *spec = nullptr) {
+                        const std::vector<LeafRec> *spec = nullptr,
+                        const Tune *tune = nullptr) {
+    if (tune) P.tune = *tune;
     P.kind = kind;
     P.dtype = dtype;
     P.esz = (int)elem_bytes(dtype);
@@ -1232,10 +1245,10 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
     // another stream of the captured graph (its steps wait for the results
     // they read through events), so independent parts of the tree overlap.
     // Memory is then never recycled, as concurrent parts would race on it.
-    constexpr int kLanes = 4;
+    const int kLanes = std::max(1, std::min(4, P.tune.max_lanes));
     P.lane.assign(NN, 0);
     int nl_used = 1;
-    if (kind == K_PR || kind == K_MAR) {
+    if ((kind == K_PR || kind == K_MAR) && kLanes > 1) {
         std::vector<double> work(NN, 0.0);
         for (int id = n; id < NN; ++id) {
             const Node &nd = pl.node[id];
@@ -1308,6 +1321,7 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
     }
     P.nlanes = nl_used;
     int64_t arena_top = plan_arena(nl_used == 1);
+    P.keep_all_elems = arena_top;
     int64_t budget = opts ? opts->hbm_budget_bytes : 0;
     size_t freeb = 0, totb = 0;
     CK(cudaMemGetInfo(&freeb, &totb));
@@ -1754,6 +1768,9 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
             }
         }
     }
+    for (auto *steps : {&P.fsteps, &P.bsteps})
+        for (auto &st : *steps)
+            if (st.kind == 2) st.ad.bps = P.tune.absorb_bps;
     trace_program(P);
     // inner offset tables of the streaming steps, one device buffer
     {
@@ -2228,6 +2245,50 @@ tn_status ensure_device(tn_model *m) {
 
 int dtype_of(tn_prec p) { return p == TN_FP64 ? 0 : 1; }
 
+tn_status check_device_error(tn_model *m);
+
+// Autotuner: build, capture and time (three graph replays after one warm-up,
+// CUDA events on the model's stream) every candidate launch shape of a
+// program, one candidate in memory at a time, and return the fastest.
+// Candidates: 4 or 1 lanes x 2, 4 or 8 blocks per SM for the streaming
+// absorb kernels.  Every candidate computes the same values (the shapes
+// change where and in which order work runs, not any kernel's arithmetic).
+tn_status autotune_program(tn_model *m, const Net &net, int kind, int dtype, int nbeta,
+                           bool grads, const tn_options *opts, Tune &best) {
+    double best_ms = 1e300;
+    bool found = false;
+    for (int lanes : {4, 1})
+        for (int bps : {4, 2, 8}) {
+            Tune c;
+            c.max_lanes = lanes;
+            c.absorb_bps = bps == 4 ? 0 : bps;
+            auto C = std::make_unique<Program>();
+            tn_status s = build_program(m, net, m->tree, kind, dtype, nbeta, grads, opts, *C,
+                                        nullptr, &c);
+            if (s == TN_E_OOM) continue;
+            if (s) return s;
+            s = capture_program(m, *C);
+            if (s) return s;
+            CK(cudaGraphLaunch(C->gexec, m->stream));
+            CK(cudaEventRecord(m->ev0, m->stream));
+            for (int r = 0; r < 3; ++r) CK(cudaGraphLaunch(C->gexec, m->stream));
+            CK(cudaEventRecord(m->ev1, m->stream));
+            CK(cudaStreamSynchronize(m->stream));
+            s = check_device_error(m);
+            if (s) return s;
+            float ms = 0;
+            CK(cudaEventElapsedTime(&ms, m->ev0, m->ev1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+                found = true;
+            }
+        }
+    if (!found) return fail(TN_E_OOM, "no candidate program fits the device memory");
+    best.tuned = true;
+    return TN_OK;
+}
+
 tn_status get_program(tn_model *m, int kind, int nbeta, const tn_options *opts, bool grads,
                       Program **out) {
     tn_status s = ensure_device(m);
@@ -2239,20 +2300,32 @@ tn_status get_program(tn_model *m, int kind, int nbeta, const tn_options *opts, 
     }
     tn_prec prec = opts ? opts->prec : TN_FP64;
     int dtype = dtype_of(prec);
-    auto key = std::make_tuple(kind, (int)prec, nbeta, grads ? 1 : 0);
+    const bool autotune = opts && opts->autotune && (kind == K_PR || kind == K_MAR);
+    auto key = std::make_tuple(kind, (int)prec, nbeta, (grads ? 1 : 0) | (autotune ? 2 : 0));
     auto it = m->progs.find(key);
     if (it != m->progs.end()) {
         *out = it->second.get();
         return TN_OK;
     }
-    auto P = std::make_unique<Program>();
     Net net = model_net(m->md, nbeta > 1, m->slice_vars);
-    s = build_program(m, net, m->tree, kind, dtype, nbeta, grads, opts, *P);
+    Tune tune;
+    if (autotune) {
+        auto tt = m->tuned.find(key);
+        if (tt != m->tuned.end()) {
+            tune = tt->second;
+        } else {
+            s = autotune_program(m, net, kind, dtype, nbeta, grads, opts, tune);
+            if (s) return s;
+            m->tuned[key] = tune;
+        }
+    }
+    auto P = std::make_unique<Program>();
+    s = build_program(m, net, m->tree, kind, dtype, nbeta, grads, opts, *P, nullptr, &tune);
     if (s == TN_E_OOM && !m->progs.empty()) {
         // release the other cached programs of this model and try once more
         m->progs.clear();
         P = std::make_unique<Program>();
-        s = build_program(m, net, m->tree, kind, dtype, nbeta, grads, opts, *P);
+        s = build_program(m, net, m->tree, kind, dtype, nbeta, grads, opts, *P, nullptr, &tune);
     }
     if (s) return s;
     s = capture_program(m, *P);
@@ -3471,6 +3544,24 @@ static tn_status profile_impl(tn_model *m, int task, int batch, const int32_t *e
     }
     CK(cudaGetLastError());
     return check_device_error(m);
+}
+
+tn_status tn_program_stats(tn_model *m, int task, int batch, const tn_options *opts,
+                           double *out) {
+    if (!m || !out || batch < 1 || (task != 0 && task != 1)) return fail(TN_E_ARG, "bad argument");
+    Program *P;
+    int sub = batch;
+    tn_status s = program_fitting(m, task == 0 ? K_PR : K_MAR, batch, opts, false, &P, &sub);
+    if (s) return s;
+    out[0] = (double)P->arena_elems * P->esz;
+    out[1] = (double)P->keep_all_elems * P->esz;
+    out[2] = P->ndrop;
+    out[3] = P->launches;
+    out[4] = P->nlanes;
+    out[5] = P->tune.absorb_bps;
+    out[6] = P->tune.tuned ? 1 : 0;
+    out[7] = sub;
+    return TN_OK;
 }
 
 double tn_last_device_ms(const tn_model *m) { return m ? m->last_ms : 0.0; }

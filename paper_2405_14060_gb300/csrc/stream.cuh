@@ -36,6 +36,7 @@ struct ADesc {
                                       // shared-label combination [nsh] (device)
     int nsh;                          // combinations of the labels W shares with X and Y
     int32_t rshc[MAXD];               // per R dim: stride in that combination index (0: not in W)
+    int bps;                          // blocks per SM of the launch (0: the kernel's default)
 };
 
 // Reduce: O[g, s, t] = sum_m X[g, m, s] Z[g, m, t]

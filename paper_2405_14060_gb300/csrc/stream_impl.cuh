@@ -309,7 +309,7 @@ static void absorb_go(const ADesc &d, int semiring, cudaStream_t st) {
             // a few resident blocks per SM, each stages W once
             constexpr int U = NS * NT <= 64 ? 2 : 1;
             int64_t ntile = d.nouter * ((d.nin + 256 * U - 1) / (256 * U));
-            int64_t cap = std::max<int64_t>(1, (152LL * 4) / std::max(1, d.nbeta));
+            int64_t cap = std::max<int64_t>(1, (152LL * (d.bps > 0 ? d.bps : 4)) / std::max(1, d.nbeta));
             dim3 grid((unsigned)std::max<int64_t>(1, std::min(ntile, cap)), (unsigned)d.nbeta, 1);
             k_absorb_sm<T, NS, NT><<<grid, 256, smem, st>>>(d);
             return;
@@ -317,7 +317,7 @@ static void absorb_go(const ADesc &d, int semiring, cudaStream_t st) {
     }
     constexpr int U = NS * NT <= 4 ? 8 : NS * NT <= 16 ? 4 : NS * NT <= 64 ? 2 : 1;
     int64_t ntile = d.nouter * ((d.nin + 256 * U - 1) / (256 * U));
-    int64_t cap = std::max<int64_t>(1, (152LL * 16) / std::max(1, d.nbeta));
+    int64_t cap = std::max<int64_t>(1, (152LL * (d.bps > 0 ? 4 * d.bps : 16)) / std::max(1, d.nbeta));
     dim3 grid((unsigned)std::max<int64_t>(1, std::min(ntile, cap)), (unsigned)d.nbeta, 1);
     if (semiring == SUM) k_absorb<T, NS, NT, SUM><<<grid, 256, 0, st>>>(d);
     else k_absorb<T, NS, NT, MAXPLUS><<<grid, 256, 0, st>>>(d);

@@ -24,7 +24,7 @@ EXPORTS = ["tn_load_model", "tn_load_model_arrays", "tn_free_model", "tn_set_ord
            "tn_mar", "tn_map", "tn_mmap", "tn_sample", "tn_pr_dev", "tn_mar_dev",
            "tn_last_device_ms", "tn_last_launch_count", "tn_last_error", "tn_contract_dev",
            "tn_profile", "tn_profile_steps", "tn_contract_dev_noalloc",
-           "tn_reassociate", "tn_choose_slices", "tn_joint_mar"]
+           "tn_reassociate", "tn_choose_slices", "tn_joint_mar", "tn_program_stats"]
 PROFILE_CLASSES = ["small", "absorb", "reduce", "tcgemm", "simtgemm", "prep", "generic", "bgemm",
                    "recompute"]
 
@@ -76,6 +76,7 @@ def lib():
             "tn_reassociate": [P, P, P, P, P],
             "tn_choose_slices": [P, P, P, D, I, P, P],
             "tn_joint_mar": [P, P, I, P, P, P, P],
+            "tn_program_stats": [P, I, I, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -101,12 +102,12 @@ def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
-def _opts(prec="fp64", budget=0, stream=None) -> Options:
+def _opts(prec="fp64", budget=0, stream=None, autotune=False) -> Options:
     o = Options()
     o.prec = PRECS[prec] if isinstance(prec, str) else int(prec)
     o.hbm_budget_bytes = int(budget)
     o.max_slices = 0
-    o.autotune = 0
+    o.autotune = 1 if autotune else 0
     o.cuda_stream = stream
     return o
 
@@ -233,18 +234,18 @@ class Model:
         e = np.ascontiguousarray(evid, np.int32)
         return e.reshape(-1, self.nvars)
 
-    def pr(self, evid=None, prec="fp64", budget=0):
+    def pr(self, evid=None, prec="fp64", budget=0, autotune=False):
         e = self._evid(evid)
         out = np.zeros(e.shape[0])
-        o = _opts(prec, budget)
+        o = _opts(prec, budget, None, autotune)
         _ck(lib().tn_pr(self._h, e.shape[0], _ptr(e), ctypes.byref(o), _ptr(out)))
         return out
 
-    def mar(self, evid=None, prec="fp64", budget=0):
+    def mar(self, evid=None, prec="fp64", budget=0, autotune=False):
         e = self._evid(evid)
         lz = np.zeros(e.shape[0])
         marg = np.zeros((e.shape[0], int(self.card.sum())))
-        o = _opts(prec, budget)
+        o = _opts(prec, budget, None, autotune)
         _ck(lib().tn_mar(self._h, e.shape[0], _ptr(e), ctypes.byref(o), _ptr(lz), _ptr(marg)))
         return lz, marg
 
@@ -294,27 +295,29 @@ class Model:
         return out
 
     # ------------------------------------------------- device-pointer forms
-    def pr_dev(self, evid, logz, tables=None, tables_are_log=False, prec="fp32", stream=None):
+    def pr_dev(self, evid, logz, tables=None, tables_are_log=False, prec="fp32", stream=None,
+               autotune=False):
         """evid, logz (and tables) are torch CUDA tensors (int32 / float64)."""
-        o = _opts(prec, 0, stream)
+        o = _opts(prec, 0, stream, autotune)
         _ck(lib().tn_pr_dev(self._h, int(evid.shape[0]), evid.data_ptr(),
                             None if tables is None else tables.data_ptr(),
                             1 if tables_are_log else 0, ctypes.byref(o), logz.data_ptr()))
 
     def mar_dev(self, evid, logz, marg, grad=None, tables=None, tables_are_log=False,
-                prec="fp32", stream=None):
-        o = _opts(prec, 0, stream)
+                prec="fp32", stream=None, autotune=False):
+        o = _opts(prec, 0, stream, autotune)
         _ck(lib().tn_mar_dev(self._h, int(evid.shape[0]), evid.data_ptr(),
                              None if tables is None else tables.data_ptr(),
                              1 if tables_are_log else 0, ctypes.byref(o), logz.data_ptr(),
                              marg.data_ptr(), None if grad is None else grad.data_ptr()))
 
-    def profile(self, task="mar", evid=None, batch=1, prec="tf32", reps=3, budget=0):
+    def profile(self, task="mar", evid=None, batch=1, prec="tf32", reps=3, budget=0,
+                autotune=False):
         """Per kernel class: ms, launches, FLOPs, bytes of one pass (averaged)."""
         e = None if evid is None else np.ascontiguousarray(evid, np.int32).reshape(-1, self.nvars)
         b = batch if e is None else e.shape[0]
         out = np.zeros(4 * len(PROFILE_CLASSES))
-        o = _opts(prec, budget)
+        o = _opts(prec, budget, None, autotune)
         _ck(lib().tn_profile(self._h, 0 if task == "pr" else 1, b,
                              None if e is None else _ptr(e), ctypes.byref(o), reps, _ptr(out)))
         res = {}
@@ -337,6 +340,16 @@ class Model:
         k = min(n.value, cap)
         rows = out[:4 * k].reshape(k, 4)
         return [(PROFILE_CLASSES[int(r[0])], r[1], r[2], r[3]) for r in rows]
+
+    def program_stats(self, task="mar", batch=1, prec="fp64", budget=0, autotune=False):
+        """tn_program_stats: facts about the program a task call runs."""
+        out = np.zeros(8)
+        o = _opts(prec, budget, None, autotune)
+        _ck(lib().tn_program_stats(self._h, 0 if task == "pr" else 1, batch, ctypes.byref(o),
+                                   _ptr(out)))
+        keys = ["arena_bytes", "keep_all_bytes", "recomputed", "launches", "lanes",
+                "absorb_blocks_per_sm", "tuned", "sub_batch"]
+        return {k: (float(v) if k.endswith("bytes") else int(v)) for k, v in zip(keys, out)}
 
     def last_device_ms(self) -> float:
         return float(lib().tn_last_device_ms(self._h))

@@ -564,6 +564,8 @@ def test_mar_checkpointing_under_budget():
     _marg_close(X, mg[0], marg_ref, 1e-10)
     prof = fresh().profile("mar", prec="fp64", reps=1, budget=b)
     assert prof.get("recompute", {}).get("launches", 0) > 0, prof
+    st = fresh().program_stats("mar", 1, "fp64", budget=b)
+    assert st["recomputed"] > 0 and st["arena_bytes"] <= b < st["keep_all_bytes"], st
     # without recomputation the same tree needs more memory: the unlimited
     # program's profile has no recompute class, and at budget b the FP32
     # program (half the bytes) needs fewer recomputations or none
@@ -571,6 +573,31 @@ def test_mar_checkpointing_under_budget():
     lz32, mg32 = fresh().mar(prec="fp32", budget=b)
     assert abs(lz32[0] - lz_ref) <= 1e-4 * abs(lz_ref)
     assert np.max(np.abs(mg32 - mg0)) < 1e-3
+
+
+def test_autotuned_program_matches_default():
+    """tn_options.autotune: the program built from the fastest of the timed
+    candidate launch shapes (graph lanes x blocks per SM of the streaming
+    kernels) computes the same FP64 values bit for bit as the default one
+    (the shapes move work between streams and blocks, not its arithmetic),
+    reports that it was tuned, and a second call reuses the choice."""
+    m = synth.grid_ising(14, 3)
+    ev = synth.evidence_batch(m, 6, 0.1, 17)
+    M = tn.Model.from_synth(m)
+    M.set_order(*M.reassociate(*M.optimize_order(0)))
+    lz0, mg0 = M.mar(ev, prec="fp64")
+    lz1, mg1 = M.mar(ev, prec="fp64", autotune=True)
+    np.testing.assert_array_equal(lz1, lz0)
+    np.testing.assert_array_equal(mg1, mg0)
+    st = M.program_stats("mar", ev.shape[0], "fp64", autotune=True)
+    assert st["tuned"] == 1 and st["lanes"] in (1, 2, 3, 4), st
+    assert st["absorb_blocks_per_sm"] in (0, 2, 8), st
+    assert M.program_stats("mar", ev.shape[0], "fp64")["tuned"] == 0
+    lzt, mgt = M.mar(ev, prec="tf32", autotune=True)
+    np.testing.assert_allclose(lzt, lz0, rtol=1e-4)
+    assert np.max(np.abs(mgt - mg0)) < 1e-3
+    lzp = M.pr(ev, prec="fp64", autotune=True)
+    np.testing.assert_allclose(lzp, lz0, rtol=0, atol=1e-10)
 
 
 def test_workload4_batched_slice():
