@@ -85,6 +85,23 @@ typedef struct {
  * Errors: TN_E_ARG (NULL arguments, unreadable file), TN_E_PARSE. */
 tn_status tn_load_model(const char *uai_path, tn_model **out);
 
+/* Read a UAI-format evidence file for model m: either one block
+ * "<nobs> v1 x1 v2 x2 ..." (one evidence set) or "<nsets>" followed by nsets
+ * such blocks (the competition's multi-sample form).  Writes the first
+ * min(max_sets, nsets) sets to evid[set][nvars] (-1 = unobserved, the layout
+ * tn_pr / tn_mar take) and the number of sets in the file to *nsets (call
+ * with max_sets = 0 to size the buffer).  Host only.  Errors: TN_E_ARG
+ * (NULL arguments, unreadable file), TN_E_PARSE (malformed file, variable or
+ * value out of range, a variable observed twice in one set). */
+tn_status tn_read_evidence(const tn_model *m, const char *path, int max_sets, int32_t *evid,
+                           int *nsets);
+
+/* Read a UAI-format MMAP query file "<nq> v1 ... vq" for model m: writes the
+ * first min(max_q, nq) query variables to query (the order tn_mmap takes)
+ * and nq to *nq.  Host only.  Errors as tn_read_evidence (TN_E_PARSE also
+ * for a repeated variable). */
+tn_status tn_read_query(const tn_model *m, const char *path, int max_q, int32_t *query, int *nq);
+
 /* Build a model from arrays.  Factor f has scope
  * scope_vars[scope_off[f] .. scope_off[f+1]) and its table starts at
  * tables + (sum of the sizes of factors 0..f-1).  All arrays are host
@@ -282,6 +299,20 @@ tn_status tn_mar_dev(tn_model *m, int batch, const int32_t *evid,
  *   evidence sets per pass (the sub-batch that fits the memory). */
 tn_status tn_program_stats(tn_model *m, int task, int batch, const tn_options *opts,
                            double *out);
+
+/* PR (task 0) or PR + MAR (task 1) for several models in one graph launch:
+ * each model's program (built and cached as tn_pr / tn_mar would, for
+ * batch[i] evidence sets evid[i] in tn_pr's layout, NULL = no evidence)
+ * becomes a branch of one CUDA graph, so models of uneven treewidth run
+ * concurrently on the device, behind a single launch on opts->cuda_stream
+ * (else the first model's stream).  Results as tn_pr / tn_mar, into host
+ * buffers logz[i][batch[i]] and, for task 1, marg[i][batch[i]][sum card].
+ * The models must be distinct, on one device, unsliced, and each batch
+ * must fit the device memory at once (no sub-batching).  Errors as tn_mar;
+ * TN_E_UNSUPPORTED for a sliced model. */
+tn_status tn_solve_multi(int task, int nmodels, tn_model *const *models, const int *batch,
+                         const int32_t *const *evid, const tn_options *opts,
+                         double *const *logz, double *const *marg);
 
 /* Device-side duration of the last task's kernels in milliseconds
  * (CUDA events around the launch on the task's stream). */

@@ -200,12 +200,44 @@ def ve_mar(model, evid=None):
     return out.value, split_marginals(model, marg)
 
 
-def ve_map(model, evid=None):
+def ve_map(model, evid=None, order=None):
+    """(MAP assignment, its log weight) by max-sum bucket elimination;
+    ``order`` (optional) is the elimination order (observed variables are
+    skipped), else min-fill."""
     m, e = _M(model), _ev(model, evid)
     x = np.zeros(m.n, np.int32)
     out = ctypes.c_double()
-    _check(_load().or_ve_map(*m.args(), _p(e), _p(x), ctypes.byref(out)), "ve_map")
+    op = None
+    if order is not None:
+        o = np.full(m.n + 1, -1, np.int32)
+        o[:len(order)] = order
+        op = _p(o)
+    _check(_load().or_ve_map(*m.args(), _p(e), op, _p(x), ctypes.byref(out)), "ve_map")
     return x, out.value
+
+
+def map_gap(model, evid=None, order=None):
+    """(MAP assignment x*, its log weight, gap): the gap is the log weight of
+    x* minus that of the best assignment that differs from x* (in FP64).  The
+    runner-up differs from x* in some free variable v, so it is the best of
+    the MAP problems with v clamped to a value other than x*_v, taken over
+    every v and value (Eq. log-map with extra evidence)."""
+    e = _ev(model, evid).copy()
+    x, lp = ve_map(model, e, order)
+    best2 = -np.inf
+    for v in range(model.nvars):
+        if e[v] >= 0:
+            continue
+        for val in range(int(model.card[v])):
+            if val == x[v]:
+                continue
+            e2 = e.copy()
+            e2[v] = val
+            try:
+                best2 = max(best2, ve_map(model, e2, order)[1])
+            except ZeroDivisionError:
+                pass
+    return x, lp, lp - best2
 
 
 def ve_mmap(model, query, evid=None):

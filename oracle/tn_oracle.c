@@ -974,12 +974,13 @@ static int decode_buckets(bte_t *B, int *x) {
 }
 
 int or_ve_map(int nvars, const int *card, int nf, const int *off, const int *sv,
-              const double *tab, const int *evid, int *assign, double *logp) {
+              const double *tab, const int *evid, const int *order_in, int *assign,
+              double *logp) {
     sliced_t S;
     int rc = slice_all(nvars, card, nf, off, sv, tab, evid, 1, &S);
     if (rc) return rc;
     int *order = (int *)malloc(sizeof(int) * (size_t)(nvars + 1));
-    int n = make_order(nvars, &S, evid, NULL, order);
+    int n = make_order(nvars, &S, evid, order_in, order);
     bte_t B;
     double lr;
     rc = bte_forward(nvars, &S, order, n, OP_MAXSUM, &B, &lr);

@@ -106,6 +106,42 @@ __device__ __forceinline__ void block_max_atomic(unsigned long long *mx, double 
     }
 }
 
+// Max-plus offsets (max-normalisation of tropical tensors): a tensor's
+// maximum is recorded under an order-preserving 64-bit key, so that
+// atomicMax orders signed values; key 0 sorts below every double and means
+// "not recorded".  A consumer subtracts the recorded maximum of each operand
+// before adding them, so stored tropical tensors stay near zero and FP32
+// rounding acts on small magnitudes; the offsets are summed in FP64.
+__device__ __forceinline__ unsigned long long okey(double d) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+// The offset of a recorded key: 0 when nothing, or a non-finite maximum (an
+// all -inf tensor), was recorded.
+template <typename T>
+__device__ __forceinline__ T okey_off(unsigned long long k) {
+    if (k == 0ull) return T(0);
+    unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    double d = __longlong_as_double((long long)b);
+    return isfinite(d) ? (T)d : T(0);
+}
+// Record the maxima of signed values: one atomic per warp when the warp's
+// lanes share an item, else one per lane.  Every lane of the warp calls it.
+__device__ __forceinline__ void record_max_key(unsigned long long *mx, int64_t beta, bool active,
+                                               double v) {
+    if (!mx) return;
+    double m = active ? v : -INFINITY;
+    long long b0 = __shfl_sync(0xffffffffu, (long long)beta, 0);
+    bool same = __all_sync(0xffffffffu, !active || beta == b0);
+    if (same) {
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, s));
+        if ((threadIdx.x & 31) == 0 && isfinite(m)) atomicMax(mx + b0, okey(m));
+    } else if (active && isfinite(m)) {
+        atomicMax(mx + beta, okey(m));
+    }
+}
+
 // Grid shape for an item-parallel kernel: blockIdx.y is the batch item and
 // blockIdx.x strides over the item's entries; about 16 blocks per SM overall.
 inline dim3 item_grid(int64_t per_item, int nbeta, int threads = 256) {

@@ -209,6 +209,7 @@ struct Program {
     char *wsX = nullptr, *wsY = nullptr, *wsD = nullptr;
     int gemm_type = 1;
     std::vector<LeafRec> leafrec;   // host copy (external sources patched per call)
+    cudaGraph_t graph = nullptr;       // the captured graph (kept for multi-model launches)
     cudaGraphExec_t gexec = nullptr;
     int launches = 0;
     int64_t marg_stride = 0, grad_stride = 0;
@@ -221,6 +222,7 @@ struct Program {
     std::vector<int> mlane_beg;                // micro subtrees of lane l: [beg[l], beg[l+1])
     ~Program() {
         if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
         for (auto e : ev) cudaEventDestroy(e);
     }
 };
@@ -1435,7 +1437,9 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
     }
     P.nleafrec = n;
     // ---- descriptors and steps
-    auto mxp = [&](int64_t i) { return maxplus ? nullptr : P.mx + i; };
+    // per-tensor maxima: power-of-two scales (sum-product) or max-plus
+    // normalisation offsets
+    auto mxp = [&](int64_t i) { return P.mx + i; };
     auto fptr = [&](int id) { return (char *)P.arena + P.fwd[id].off * P.esz; };
     auto aptr = [&](int id) { return (char *)P.arena + P.adj[id].off * P.esz; };
     // forward tensors as the backward pass reads them (dropped ones from
@@ -1869,8 +1873,8 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
     // ---- leaf records to device
     CK(P.mem.alloc(&P.d_leaf, sizeof(LeafRec) * n));
     CK(cudaMemcpy(P.d_leaf, P.leafrec.data(), sizeof(LeafRec) * n, cudaMemcpyHostToDevice));
-    // ---- exponent list for log Z
-    if (!maxplus) {
+    // ---- exponent (sum-product) or offset (max-plus) list for log Z
+    {
         std::vector<int64_t> ex;
         for (int id = 0; id < NN; ++id) {
             if (id == pl.root) continue;
@@ -2204,7 +2208,7 @@ tn_status capture_program(tn_model *m, Program &P) {
     cudaError_t e = cudaStreamEndCapture(m->stream, &g);
     if (e != cudaSuccess) return fail(TN_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
     e = cudaGraphInstantiate(&P.gexec, g, 0);
-    cudaGraphDestroy(g);
+    P.graph = g;
     if (e != cudaSuccess) return fail(TN_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
     return TN_OK;
 }
@@ -2552,6 +2556,32 @@ tn_status tn_load_model(const char *uai_path, tn_model **out) {
     return TN_OK;
 }
 
+tn_status tn_read_evidence(const tn_model *m, const char *path, int max_sets, int32_t *evid,
+                           int *nsets) {
+    if (!m || !path || !nsets || max_sets < 0 || (max_sets > 0 && !evid))
+        return fail(TN_E_ARG, "bad argument");
+    std::vector<std::vector<int32_t>> sets;
+    bool perr = false;
+    std::string err = evidence_from_uai(path, m->md, sets, perr);
+    if (!err.empty()) return fail(perr ? TN_E_PARSE : TN_E_ARG, err);
+    *nsets = (int)sets.size();
+    for (int b = 0; b < std::min<int>(max_sets, (int)sets.size()); ++b)
+        std::copy(sets[b].begin(), sets[b].end(), evid + (size_t)b * m->md.nvars);
+    return TN_OK;
+}
+
+tn_status tn_read_query(const tn_model *m, const char *path, int max_q, int32_t *query, int *nq) {
+    if (!m || !path || !nq || max_q < 0 || (max_q > 0 && !query))
+        return fail(TN_E_ARG, "bad argument");
+    std::vector<int32_t> q;
+    bool perr = false;
+    std::string err = query_from_uai(path, m->md, q, perr);
+    if (!err.empty()) return fail(perr ? TN_E_PARSE : TN_E_ARG, err);
+    *nq = (int)q.size();
+    std::copy(q.begin(), q.begin() + std::min<int>(max_q, (int)q.size()), query);
+    return TN_OK;
+}
+
 tn_status tn_load_model_arrays(int nvars, const int *card, int nfactors, const int *scope_off,
                                const int *scope_vars, const double *tables, tn_model **out) {
     if (!out) return fail(TN_E_ARG, "NULL output");
@@ -2853,6 +2883,92 @@ static tn_status mar_common(tn_model *m, int batch, const int32_t *evid, bool de
 tn_status tn_mar(tn_model *m, int batch, const int32_t *evid, const tn_options *opts, double *logz,
                  double *marg) {
     return mar_common(m, batch, evid, false, nullptr, 0, opts, logz, marg, nullptr);
+}
+
+// Several models in one launch: each model's captured program becomes a
+// child graph of one parent graph (independent branches, so the device runs
+// them concurrently: a model of small treewidth no longer pays a launch and
+// an idle GPU of its own), launched once on one stream.
+tn_status tn_solve_multi(int task, int nmodels, tn_model *const *models, const int *batch,
+                         const int32_t *const *evid, const tn_options *opts,
+                         double *const *logz, double *const *marg) {
+    if (nmodels < 1 || !models || !batch || !logz || (task != 0 && task != 1) ||
+        (task == 1 && !marg))
+        return fail(TN_E_ARG, "bad argument");
+    std::vector<Program *> progs(nmodels);
+    int dev = -1;
+    for (int i = 0; i < nmodels; ++i) {
+        tn_model *m = models[i];
+        if (!m || batch[i] < 1 || !logz[i] || (task == 1 && !marg[i]))
+            return fail(TN_E_ARG, "bad argument for model " + std::to_string(i));
+        for (int j = 0; j < i; ++j)
+            if (models[j] == m) return fail(TN_E_ARG, "a model appears twice");
+        if (!m->slice_vars.empty()) return fail(TN_E_UNSUPPORTED, "sliced model in a multi-model launch");
+        tn_status s = check_evid(m, batch[i], evid ? evid[i] : nullptr);
+        if (s) return s;
+        s = get_program(m, task == 0 ? K_PR : K_MAR, batch[i], opts, false, &progs[i]);
+        if (s) return s;
+        if (dev < 0) dev = m->device;
+        else if (m->device != dev) return fail(TN_E_ARG, "models on different devices");
+        s = override_tables(m, nullptr, 0, m->stream);
+        if (s) return s;
+    }
+    cudaStream_t st = opts && opts->cuda_stream ? (cudaStream_t)opts->cuda_stream : models[0]->stream;
+    for (int i = 0; i < nmodels; ++i) CK(cudaStreamSynchronize(models[i]->stream));
+    cudaGraph_t parent = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    CK(cudaGraphCreate(&parent, 0));
+    tn_status rs = TN_OK;
+    for (int i = 0; i < nmodels && rs == TN_OK; ++i) {
+        cudaGraphNode_t node;
+        cudaError_t e = cudaGraphAddChildGraphNode(&node, parent, nullptr, 0, progs[i]->graph);
+        if (e != cudaSuccess) rs = fail(TN_E_CUDA, std::string("child graph: ") + cudaGetErrorString(e));
+    }
+    if (rs == TN_OK) {
+        cudaError_t e = cudaGraphInstantiate(&exec, parent, 0);
+        if (e != cudaSuccess) rs = fail(TN_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    if (rs == TN_OK) {
+        for (int i = 0; i < nmodels; ++i) {
+            Program *P = progs[i];
+            size_t eb = (size_t)P->nbeta * models[i]->md.nvars * 4;
+            if (!eb) continue;
+            if (evid && evid[i])
+                CK(cudaMemcpyAsync(P->d_evid, evid[i], eb, cudaMemcpyHostToDevice, st));
+            else
+                CK(cudaMemsetAsync(P->d_evid, 0xff, eb, st));
+        }
+        CK(cudaEventRecord(models[0]->ev0, st));
+        CK(cudaGraphLaunch(exec, st));
+        CK(cudaEventRecord(models[0]->ev1, st));
+        for (int i = 0; i < nmodels; ++i) {
+            Program *P = progs[i];
+            CK(cudaMemcpyAsync(logz[i], P->d_logz, (size_t)batch[i] * 8, cudaMemcpyDeviceToHost, st));
+            if (task == 1)
+                CK(cudaMemcpyAsync(marg[i], P->d_marg, (size_t)batch[i] * P->marg_stride * 8,
+                                   cudaMemcpyDeviceToHost, st));
+        }
+        CK(cudaStreamSynchronize(st));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, models[0]->ev0, models[0]->ev1));
+        int64_t nl = 0;
+        for (int i = 0; i < nmodels; ++i) nl += progs[i]->launches;
+        for (int i = 0; i < nmodels && rs == TN_OK; ++i) {
+            models[i]->last_ms = ms;
+            models[i]->last_launches = nl;
+            rs = check_device_error(models[i]);
+        }
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(parent);
+    if (rs) return rs;
+    if (task == 1)
+        for (int i = 0; i < nmodels; ++i)
+            for (int b = 0; b < batch[i]; ++b)
+                if (!(logz[i][b] > -INFINITY))
+                    return fail(TN_E_ARG, "p(e) = 0 for evidence set " + std::to_string(b) +
+                                              " of model " + std::to_string(i));
+    return TN_OK;
 }
 
 tn_status tn_mar_dev(tn_model *m, int batch, const int32_t *evid, const double *factor_tables,

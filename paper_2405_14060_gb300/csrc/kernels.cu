@@ -70,9 +70,14 @@ __global__ void __launch_bounds__(256) k_contract(const __grid_constant__ CDesc 
     const int64_t beta = blockIdx.y;
     T mx = 0;
     T sa = T(1), sb = T(1);
+    // max-plus: operands max-normalised by their recorded maxima
+    T oa_ = T(0), ob_ = T(0), mxq = -INFINITY;
     if (SEMI == SUM) {
         sa = d.mxa ? pow2neg<T>(exp_of_bits(d.mxa[beta * d.mxa_bs])) : T(1);
         sb = d.mxb ? pow2neg<T>(exp_of_bits(d.mxb[beta * d.mxb_bs])) : T(1);
+    } else {
+        oa_ = d.mxa ? okey_off<T>(d.mxa[beta * d.mxa_bs]) : T(0);
+        ob_ = d.mxb ? okey_off<T>(d.mxb[beta * d.mxb_bs]) : T(0);
     }
     for (int64_t o = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; o < d.nout_total;
          o += (int64_t)gridDim.x * blockDim.x) {
@@ -102,26 +107,28 @@ __global__ void __launch_bounds__(256) k_contract(const __grid_constant__ CDesc 
             T best = -INFINITY;
             int32_t bk = 0;
             if (d.nk == 0) {
-                best = A[0] + B[0];
+                best = (A[0] - oa_) + (B[0] - ob_);
             } else if (d.nk == 1) {
                 int64_t sA = d.ksa[0], sB = d.ksb[0];
                 for (int64_t k = 0; k < d.ktotal; ++k) {
-                    T v = A[k * sA] + B[k * sB];
+                    T v = (A[k * sA] - oa_) + (B[k * sB] - ob_);
                     if (v > best) { best = v; bk = (int32_t)k; }
                 }
             } else {
                 for (int64_t k = 0; k < d.ktotal; ++k) {
                     int64_t ka, kb;
                     decode_k(d, k, ka, kb);
-                    T v = A[ka] + B[kb];
+                    T v = (A[ka] - oa_) + (B[kb] - ob_);
                     if (v > best) { best = v; bk = (int32_t)k; }
                 }
             }
             ((T *)d.C)[idx] = best;
             if (d.argmax) d.argmax[idx] = bk;
+            mxq = mxq > best ? mxq : best;
         }
     }
     if (SEMI == SUM && d.mxc) block_max_atomic(d.mxc + beta, (double)mx);
+    if (SEMI == MAXPLUS) record_max_key(d.mxc, beta, true, (double)mxq);
 }
 
 // ---------------------------------------------------------------- split-K
@@ -162,12 +169,14 @@ __global__ void __launch_bounds__(256) k_contract_splitk(const __grid_constant__
             if (lane == 0) part[oy * nchunks + blockIdx.x] = v;
         }
     } else {
+        const T oa_ = d.mxa ? okey_off<T>(d.mxa[beta * d.mxa_bs]) : T(0);
+        const T ob_ = d.mxb ? okey_off<T>(d.mxb[beta * d.mxb_bs]) : T(0);
         T best = -INFINITY;
         int32_t bk = INT32_MAX;
         for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
             int64_t ka, kb;
             decode_k(d, k, ka, kb);
-            T s = A[ka] + B[kb];
+            T s = (A[ka] - oa_) + (B[kb] - ob_);
             if (s > best || (s == best && (int32_t)k < bk)) { best = s; bk = (int32_t)k; }
         }
         // (max, lowest index) reduction
@@ -227,6 +236,7 @@ __global__ void __launch_bounds__(256) k_splitk_reduce(const __grid_constant__ C
         ((T *)d.C)[oy] = val;
     }
     if (SEMI == SUM) record_max(d.mxc, beta, active, (double)val);
+    else record_max_key(d.mxc, beta, active, (double)val);
 }
 
 static constexpr int64_t kTargetThreads = 152LL * 2048;

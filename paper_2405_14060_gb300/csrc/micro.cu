@@ -23,8 +23,7 @@ __global__ void __launch_bounds__(256) k_micro(const MicroDesc *__restrict__ nod
         const MicroDesc &d = nodes[i];
         const int nb = d.nbeta, nout = d.nout_total;
         T tmax = 0;   // single item: this thread's maximum, reduced once per node
-        if (SEMI == SUM)
-            for (int b = threadIdx.x; b < nb; b += blockDim.x) smx[b] = 0ull;
+        for (int b = threadIdx.x; b < nb; b += blockDim.x) smx[b] = 0ull;
         __syncthreads();
         for (int idx = threadIdx.x; idx < nb * nout; idx += blockDim.x) {
             int beta = idx / nout, o = idx - beta * nout;
@@ -76,6 +75,9 @@ __global__ void __launch_bounds__(256) k_micro(const MicroDesc *__restrict__ nod
                     else if (acc > T(0)) atomicMax(&smx[beta], dbits((double)acc));
                 }
             } else {
+                // operands max-normalised by their recorded maxima
+                const T oa_ = d.mxa >= 0 ? okey_off<T>(mx[d.mxa + beta * d.mxa_bs]) : T(0);
+                const T ob_ = d.mxb >= 0 ? okey_off<T>(mx[d.mxb + beta * d.mxb_bs]) : T(0);
                 T best = -INFINITY;
                 int32_t bk = 0;
                 for (int k = 0; k < d.ktotal; ++k) {
@@ -86,11 +88,12 @@ __global__ void __launch_bounds__(256) k_micro(const MicroDesc *__restrict__ nod
                         ka += dg * d.ksa[q];
                         kb += dg * d.ksb[q];
                     }
-                    T v = A[ka] + B[kb];
+                    T v = (A[ka] - oa_) + (B[kb] - ob_);
                     if (v > best) { best = v; bk = k; }
                 }
                 arena[d.offC + idx] = best;
                 if (d.amoff >= 0) am[d.amoff + idx] = bk;
+                if (d.mxc >= 0 && isfinite((double)best)) atomicMax(&smx[beta], okey((double)best));
             }
         }
         if (SEMI == SUM && d.mxc >= 0 && nb == 1) {
@@ -103,7 +106,7 @@ __global__ void __launch_bounds__(256) k_micro(const MicroDesc *__restrict__ nod
             if ((threadIdx.x & 31) == 0 && tmax > T(0)) atomicMax(&smx[0], dbits((double)tmax));
         }
         __syncthreads();
-        if (SEMI == SUM && d.mxc >= 0)
+        if (d.mxc >= 0)
             for (int b = threadIdx.x; b < nb; b += blockDim.x) mx[d.mxc + b] = smx[b];
         __syncthreads();
     }

@@ -1,6 +1,7 @@
 // Model input: UAI text parsing and validation of array input (host).
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <fstream>
 #include <sstream>
@@ -114,6 +115,129 @@ std::string model_from_uai(const char *path, ModelData &m, bool &parse_error) {
         }
     }
     return model_from_arrays(n, card.data(), nf, off.data(), sv.data(), tab.data(), m);
+}
+
+static bool read_ints(const char *path, std::vector<long long> &t, std::string &err) {
+    std::ifstream in(path);
+    if (!in) {
+        err = std::string("cannot open ") + path;
+        return false;
+    }
+    std::string tok;
+    while (in >> tok) {
+        char *end = nullptr;
+        long long v = std::strtoll(tok.c_str(), &end, 10);
+        if (!end || *end) {
+            err = "not an integer: " + tok;
+            return false;
+        }
+        t.push_back(v);
+    }
+    return true;
+}
+
+// One block "<nobs> v1 x1 ..." starting at t[p]; false if it does not fit.
+static bool evidence_block(const std::vector<long long> &t, size_t &p, size_t end) {
+    if (p >= end || t[p] < 0) return false;
+    long long k = t[p];
+    if ((long long)(end - p - 1) < 2 * k) return false;
+    p += 1 + 2 * (size_t)k;
+    return true;
+}
+
+std::string evidence_from_uai(const char *path, const ModelData &m,
+                              std::vector<std::vector<int32_t>> &sets, bool &parse_error) {
+    parse_error = false;
+    sets.clear();
+    std::vector<long long> t;
+    std::string err;
+    if (!read_ints(path, t, err)) {
+        parse_error = err.rfind("cannot open", 0) != 0;
+        return err;
+    }
+    if (t.empty()) {
+        parse_error = true;
+        return "empty evidence file";
+    }
+    // several sets when "<nsets>" and exactly that many blocks fill the file
+    std::vector<std::pair<size_t, size_t>> blocks;   // (start, end) of each block
+    bool multi = false;
+    if (t[0] >= 0) {
+        size_t p = 1;
+        std::vector<std::pair<size_t, size_t>> b;
+        long long n = t[0];
+        bool ok = true;
+        for (long long i = 0; i < n && ok; ++i) {
+            size_t s0 = p;
+            ok = evidence_block(t, p, t.size());
+            if (ok) b.push_back({s0, p});
+        }
+        if (ok && p == t.size() && !(n == 0 && t.size() == 1)) {
+            multi = true;
+            blocks = b;
+        }
+    }
+    if (!multi) {
+        size_t p = 0;
+        if (!evidence_block(t, p, t.size()) || p != t.size()) {
+            parse_error = true;
+            return "evidence file is neither one block \"<nobs> var value ...\" nor a "
+                   "count of such blocks followed by them";
+        }
+        blocks.push_back({0, p});
+    }
+    for (auto &b : blocks) {
+        std::vector<int32_t> row(m.nvars, -1);
+        long long k = t[b.first];
+        for (long long i = 0; i < k; ++i) {
+            long long v = t[b.first + 1 + 2 * i], x = t[b.first + 2 + 2 * i];
+            if (v < 0 || v >= m.nvars) {
+                parse_error = true;
+                return "evidence variable out of range: " + std::to_string(v);
+            }
+            if (x < 0 || x >= m.card[v]) {
+                parse_error = true;
+                return "evidence value out of range for variable " + std::to_string(v);
+            }
+            if (row[v] >= 0) {
+                parse_error = true;
+                return "evidence repeats variable " + std::to_string(v);
+            }
+            row[v] = (int32_t)x;
+        }
+        sets.push_back(row);
+    }
+    return "";
+}
+
+std::string query_from_uai(const char *path, const ModelData &m, std::vector<int32_t> &q,
+                           bool &parse_error) {
+    parse_error = false;
+    q.clear();
+    std::vector<long long> t;
+    std::string err;
+    if (!read_ints(path, t, err)) {
+        parse_error = err.rfind("cannot open", 0) != 0;
+        return err;
+    }
+    if (t.empty() || t[0] < 0 || (long long)t.size() != 1 + t[0]) {
+        parse_error = true;
+        return "query file must be \"<nq> v1 ... vq\"";
+    }
+    std::vector<char> seen(m.nvars, 0);
+    for (size_t i = 1; i < t.size(); ++i) {
+        if (t[i] < 0 || t[i] >= m.nvars) {
+            parse_error = true;
+            return "query variable out of range: " + std::to_string(t[i]);
+        }
+        if (seen[t[i]]) {
+            parse_error = true;
+            return "query repeats variable " + std::to_string(t[i]);
+        }
+        seen[t[i]] = 1;
+        q.push_back((int32_t)t[i]);
+    }
+    return "";
 }
 
 }  // namespace tn

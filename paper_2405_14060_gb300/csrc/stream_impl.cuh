@@ -41,10 +41,16 @@ __global__ void __launch_bounds__(256) k_absorb(const __grid_constant__ ADesc d)
     const int64_t beta = blockIdx.y;
     T mx = 0;
     T scale = T(1);
+    // max-plus: the operands' recorded maxima are subtracted (max-normalised
+    // inputs) and the output's maximum is recorded
+    T offx = T(0), offw = T(0), mxq = -INFINITY;
     if (SEMI == SUM) {
         T sx = d.mxx ? pow2neg<T>(exp_of_bits(d.mxx[beta * d.mxx_bs])) : T(1);
         T sw = d.mxw ? pow2neg<T>(exp_of_bits(d.mxw[beta * d.mxw_bs])) : T(1);
         scale = sx * sw;
+    } else {
+        offx = d.mxx ? okey_off<T>(d.mxx[beta * d.mxx_bs]) : T(0);
+        offw = d.mxw ? okey_off<T>(d.mxw[beta * d.mxw_bs]) : T(0);
     }
     // tiles: (outer index, chunk of 256 U inner positions)
     const int nch = (nin + 256 * U - 1) / (256 * U);
@@ -110,7 +116,7 @@ __global__ void __launch_bounds__(256) k_absorb(const __grid_constant__ ADesc d)
                 ow[u] = __ldg(tw + jj);
 #pragma unroll
                 for (int s = 0; s < NS; ++s)
-                    x[u][s] = (on[u] && (NS == 1 || s < d.ns)) ? Xb[ox + d.xoff[s]] : T(0);
+                    x[u][s] = (on[u] && (NS == 1 || s < d.ns)) ? Xb[ox + d.xoff[s]] - offx : T(0);
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
@@ -133,10 +139,11 @@ __global__ void __launch_bounds__(256) k_absorb(const __grid_constant__ ADesc d)
 #pragma unroll
                         for (int s = 0; s < NS; ++s) {
                             if (NS > 1 && s >= d.ns) break;
-                            T v = x[u][s] + __ldg(W + d.wso[s] + d.wto[t]);
+                            T v = x[u][s] + (__ldg(W + d.wso[s] + d.wto[t]) - offw);
                             if (v > best) { best = v; bk = s; }
                         }
                         Y[d.yoff[t]] = best;
+                        mxq = mxq > best ? mxq : best;
                         if (d.argmax) d.argmax[by + oy[u] + d.yoff[t]] = bk;
                     }
                 }
@@ -144,6 +151,7 @@ __global__ void __launch_bounds__(256) k_absorb(const __grid_constant__ ADesc d)
         }
     }
     if (SEMI == SUM && d.mxy) block_max_atomic(d.mxy + beta, (double)mx * (double)scale);
+    if (SEMI == MAXPLUS) record_max_key(d.mxy, beta, true, (double)mxq);
 }
 
 // Sum-product absorb with many (summed x new) combinations per position.

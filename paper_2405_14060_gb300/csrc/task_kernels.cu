@@ -5,6 +5,7 @@
 #include <cfloat>
 #include <cmath>
 
+#include "devutil.cuh"
 #include "task_kernels.cuh"
 
 namespace tn {
@@ -29,7 +30,7 @@ __global__ void k_leaves(const LeafRec *recs, const double *tables, const int *c
     T *dst = base + r.dst;
     __shared__ double smax[32];
     if (r.kind == LEAF_FACTOR || r.kind == LEAF_EXTERNAL) {
-        double m = 0.0;
+        double m = log_mode ? -INFINITY : 0.0;
         for (int64_t i = threadIdx.x; i < r.size; i += blockDim.x) {
             double x;
             if (r.kind == LEAF_FACTOR) {
@@ -55,18 +56,19 @@ __global__ void k_leaves(const LeafRec *recs, const double *tables, const int *c
                 x = v > 0 ? log(v) + sig * 0.69314718055994530942 : -INFINITY;
             }
             dst[i] = (T)x;
-            if (!log_mode) m = fmax(m, x);
+            m = fmax(m, log_mode ? (double)(T)x : x);
         }
-        if (!log_mode) {
+        // the maximum: a power-of-two scale source for sum-product, the
+        // max-normalisation offset (order-preserving key) for max-plus
 #pragma unroll
-            for (int s = 16; s > 0; s >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, s));
-            if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = m;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                double t = 0;
-                for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, smax[w]);
-                mx[r.mx] = (unsigned long long)__double_as_longlong(t);
-            }
+        for (int s = 16; s > 0; s >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, s));
+        if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = log_mode ? -INFINITY : 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, smax[w]);
+            mx[r.mx] = log_mode ? (isfinite(t) ? okey(t) : 0ull)
+                                : (unsigned long long)__double_as_longlong(t);
         }
     } else {
         int v = r.var, c = card[v];
@@ -193,7 +195,24 @@ __global__ void __launch_bounds__(256) k_logz(int nbeta, const T *root, int root
     const int b = blockIdx.x;
     const double r = (double)root[root_beta ? b : 0];
     if (maxplus) {
-        if (threadIdx.x == 0) logz[b] = r;
+        // log p = root + the offsets every consumer subtracted (FP64 sum in a
+        // fixed order: per-thread strided sums, then a fixed tree)
+        double s = 0.0;
+        for (int i = threadIdx.x; i < nexp; i += blockDim.x) {
+            int64_t idx = exps[2 * i], bs = exps[2 * i + 1];
+            s += okey_off<double>(mx[idx + (bs ? b : 0)]);
+        }
+        __shared__ double dpart[8];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) dpart[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += dpart[w];
+            logz[b] = r + t;
+            if (sigma_out) sigma_out[b] = t;
+        }
         return;
     }
     long long s = 0;

@@ -332,6 +332,26 @@ def write_uai(model: Model, path_or_buf) -> None:
             f.write(text)
 
 
+def write_evidence(evid, path) -> None:
+    """Write evidence sets (int [nsets, nvars] or [nvars], -1 = unobserved) in
+    the UAI multi-sample evidence format: "<nsets>" then, per set,
+    "<nobs> v1 x1 v2 x2 ..."."""
+    e = np.atleast_2d(np.asarray(evid))
+    lines = [str(e.shape[0])]
+    for row in e:
+        obs = np.nonzero(row >= 0)[0]
+        lines.append(" ".join([str(len(obs))] + [f"{int(v)} {int(row[v])}" for v in obs]))
+    with open(path, "w") as f:
+        f.write("\n".join(lines) + "\n")
+
+
+def write_query(query, path) -> None:
+    """Write an MMAP query in the UAI query format: "<nq> v1 ... vq"."""
+    q = [int(v) for v in query]
+    with open(path, "w") as f:
+        f.write(" ".join([str(len(q))] + [str(v) for v in q]) + "\n")
+
+
 def read_uai(path: str) -> Model:
     with open(path) as f:
         toks = f.read().split()

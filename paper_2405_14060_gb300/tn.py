@@ -24,7 +24,8 @@ EXPORTS = ["tn_load_model", "tn_load_model_arrays", "tn_free_model", "tn_set_ord
            "tn_mar", "tn_map", "tn_mmap", "tn_sample", "tn_pr_dev", "tn_mar_dev",
            "tn_last_device_ms", "tn_last_launch_count", "tn_last_error", "tn_contract_dev",
            "tn_profile", "tn_profile_steps", "tn_contract_dev_noalloc",
-           "tn_reassociate", "tn_choose_slices", "tn_joint_mar", "tn_program_stats"]
+           "tn_reassociate", "tn_choose_slices", "tn_joint_mar", "tn_program_stats",
+           "tn_read_evidence", "tn_read_query", "tn_solve_multi"]
 PROFILE_CLASSES = ["small", "absorb", "reduce", "tcgemm", "simtgemm", "prep", "generic", "bgemm",
                    "recompute"]
 
@@ -77,6 +78,9 @@ def lib():
             "tn_choose_slices": [P, P, P, D, I, P, P],
             "tn_joint_mar": [P, P, I, P, P, P, P],
             "tn_program_stats": [P, I, I, P, P],
+            "tn_read_evidence": [P, ctypes.c_char_p, I, P, P],
+            "tn_read_query": [P, ctypes.c_char_p, I, P, P],
+            "tn_solve_multi": [I, I, P, P, P, P, P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -169,6 +173,22 @@ class Model:
                 lib().tn_free_model(self._h)
         except Exception:
             pass
+
+    def read_evidence(self, path: str) -> np.ndarray:
+        """Evidence sets of a UAI evidence file: int32 [nsets, nvars], -1 = free."""
+        n = ctypes.c_int()
+        _ck(lib().tn_read_evidence(self._h, path.encode(), 0, None, ctypes.byref(n)))
+        out = np.zeros((max(1, n.value), self.nvars), np.int32)
+        _ck(lib().tn_read_evidence(self._h, path.encode(), n.value, _ptr(out), ctypes.byref(n)))
+        return out[:n.value]
+
+    def read_query(self, path: str) -> np.ndarray:
+        """Query variables of a UAI MMAP query file."""
+        n = ctypes.c_int()
+        _ck(lib().tn_read_query(self._h, path.encode(), 0, None, ctypes.byref(n)))
+        out = np.zeros(max(1, n.value), np.int32)
+        _ck(lib().tn_read_query(self._h, path.encode(), n.value, _ptr(out), ctypes.byref(n)))
+        return out[:n.value]
 
     # ------------------------------------------------------------ orders
     def set_order(self, left=None, right=None, slice_vars: Sequence[int] = ()):
@@ -356,6 +376,25 @@ class Model:
 
     def last_launch_count(self) -> int:
         return int(lib().tn_last_launch_count(self._h))
+
+
+def solve_multi(models, evids, task="mar", prec="fp64", autotune=False):
+    """tn_solve_multi: PR ("pr") or PR + MAR ("mar") of several models in one
+    graph launch.  evids[i]: int32 [batch, nvars] (or None: one set, no
+    evidence).  Returns [(logz, marg or None) per model]."""
+    n = len(models)
+    evs = [m._evid(e) for m, e in zip(models, evids)]
+    hs = (ctypes.c_void_p * n)(*[m._h for m in models])
+    bt = np.array([e.shape[0] for e in evs], np.int32)
+    ep = (ctypes.c_void_p * n)(*[e.ctypes.data for e in evs])
+    lz = [np.zeros(e.shape[0]) for e in evs]
+    mg = [np.zeros((e.shape[0], int(m.card.sum()))) for m, e in zip(models, evs)]
+    lp = (ctypes.c_void_p * n)(*[a.ctypes.data for a in lz])
+    mp = (ctypes.c_void_p * n)(*[a.ctypes.data for a in mg])
+    o = _opts(prec, 0, None, autotune)
+    _ck(lib().tn_solve_multi(1 if task == "mar" else 0, n, hs, _ptr(bt), ep, ctypes.byref(o),
+                             lp, mp))
+    return [(a, b if task == "mar" else None) for a, b in zip(lz, mg)]
 
 
 def _contract_args(sizes, la, A, lb, B, lc, C, argmax):

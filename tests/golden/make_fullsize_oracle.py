@@ -12,8 +12,12 @@ the full-size parity tests and the accuracy figures of the benchmark:
   spins observed in each): log p(e) for a seeded subset of the sets by
   bucket elimination with the oracle's min-fill order, and for each of them
   p(s_v | e) of a few seeded unobserved spins by conditioning.
+* MAP (Eq. log-map) of a 20x20 grid Ising model (400 spins, seed 20240620)
+  by max-sum elimination along the row sweep, and of the 300-variable
+  Bayesian network with its evidence: the assignment, its log weight and the
+  gap to the best assignment that differs from it (oracle.map_gap).
 
-    python tests/golden/make_fullsize_oracle.py     # a few minutes on 8 cores
+    python tests/golden/make_fullsize_oracle.py [section ...]   # all: ~35 min on 8 cores
 """
 import json
 import os
@@ -65,9 +69,35 @@ def rrg200_batched():
     return out
 
 
+def grid20_map():
+    m = synth.grid_ising(20, 20240620)
+    t0 = time.time()
+    x, lp, gap = oracle.map_gap(m, order=np.arange(m.nvars))
+    print(f"grid20 MAP: log p = {lp:.12f}, gap {gap:.3e}, {time.time() - t0:.0f} s", flush=True)
+    return {"workload": "grid20x20 Ising, seed 20240620", "order": "row sweep",
+            "assign": [int(v) for v in x], "logp": lp, "gap": gap}
+
+
+def bn300_map():
+    w = synth.workload(3)
+    t0 = time.time()
+    x, lp, gap = oracle.map_gap(w.model, w.evid[0])
+    print(f"bn300 MAP: log p = {lp:.12f}, gap {gap:.3e}, {time.time() - t0:.0f} s", flush=True)
+    return {"workload": "300-variable banded Bayesian network, seed 20240525, 20% observed",
+            "order": "oracle min-fill", "assign": [int(v) for v in x], "logp": lp, "gap": gap}
+
+
+SECTIONS = {"grid24": grid24, "rrg200_batched": rrg200_batched, "grid20_map": grid20_map,
+            "bn300_map": bn300_map}
+
+
 def main():
-    res = {"note": "written by tests/golden/make_fullsize_oracle.py from the CPU FP64 oracle",
-           "grid24": grid24(), "rrg200_batched": rrg200_batched()}
+    res = {"note": "written by tests/golden/make_fullsize_oracle.py from the CPU FP64 oracle"}
+    if os.path.exists(OUT):
+        with open(OUT) as f:
+            res.update(json.load(f))
+    for name in (sys.argv[1:] or list(SECTIONS)):
+        res[name] = SECTIONS[name]()
     with open(OUT, "w") as f:
         json.dump(res, f, indent=1)
     print("wrote", OUT)

@@ -160,6 +160,49 @@ def test_map_small_and_workload3():
         assert abs(oracle.log_weight(m, x) - lo) < 1e-9
 
 
+# Worst-case FP32 rounding of a max-normalised tropical contraction over these
+# trees: each root entry is a chain of at most ~1000 additions whose operands
+# stay below 32 in magnitude after normalisation, 0.5 ulp(32) = 1.9e-6 each.
+FP32_MAXPLUS_BOUND = 1000 * 2.0 ** -19
+
+
+def _same_map_or_tie(m, x, ref, bound):
+    """The GPU's MAP assignment is the oracle's, or (certificate) the oracle's
+    runner-up gap is within the rounding bound and x scores within it."""
+    if np.array_equal(x, np.asarray(ref["assign"])):
+        return
+    lw = oracle.log_weight(m, x)
+    assert ref["gap"] <= bound and ref["logp"] - lw <= bound, (ref["gap"], ref["logp"] - lw)
+
+
+def test_map_at_size_against_oracle():
+    """MAP with tropical tensors of 2^21 entries: a 20 x 20 grid Ising model
+    on the library's greedy tree, FP64 and FP32 max-plus, against the
+    oracle's stored MAP (max-sum elimination along the row sweep); and the
+    300-variable Bayesian network.  The oracle's stored gap to the runner-up
+    assignment certifies FP32 exactness (it must exceed the FP32 bound of the
+    max-normalised contraction, else a tie within rounding is accepted)."""
+    g = _golden()
+    ref = g["grid20_map"]
+    m = synth.grid_ising(20, 20240620)
+    M = tn.Model.from_synth(m)
+    M.set_order(*M.optimize_order(0))
+    assert M.tree_stats(1, "fp32")["sc"] >= 20
+    x64, lp64 = M.map(prec="fp64")
+    np.testing.assert_array_equal(x64, ref["assign"])
+    assert abs(lp64 - ref["logp"]) < 1e-9
+    x32, lp32 = M.map(prec="fp32")
+    _same_map_or_tie(m, x32, ref, FP32_MAXPLUS_BOUND)
+    assert abs(lp32 - ref["logp"]) <= FP32_MAXPLUS_BOUND
+    rb = g["bn300_map"]
+    w = synth.workload(3)
+    B = tn.Model.from_synth(w.model)
+    for prec, bound in (("fp64", 1e-9), ("fp32", FP32_MAXPLUS_BOUND)):
+        x, lp = B.map(w.evid[0], prec=prec)
+        _same_map_or_tie(w.model, x, rb, bound)
+        assert abs(lp - rb["logp"]) <= bound
+
+
 def test_mmap_small_and_workload3():
     for seed in range(3):
         m = synth.bayes_net(14, 40 + seed)
@@ -598,6 +641,69 @@ def test_autotuned_program_matches_default():
     assert np.max(np.abs(mgt - mg0)) < 1e-3
     lzp = M.pr(ev, prec="fp64", autotune=True)
     np.testing.assert_allclose(lzp, lz0, rtol=0, atol=1e-10)
+
+
+def test_uai_files_through_tasks(tmp_path):
+    """A model, its evidence sets and an MMAP query read from UAI-format
+    files (tn_load_model, tn_read_evidence, tn_read_query) give the oracle's
+    results: PR / MAR in FP64 within 1e-10 for every set, MAP and MMAP
+    assignments exact; the 300-variable Bayesian network of the MAP workload
+    read from files gives the oracle's MAP assignment."""
+    m = synth.bayes_net(14, 21)
+    ev = synth.evidence_batch(m, 4, 0.2, 5)
+    q = synth.mmap_query(m, ev[0], 0.4, np.random.default_rng(3))
+    pu, pe, pq = (str(tmp_path / x) for x in ("m.uai", "m.uai.evid", "m.uai.query"))
+    synth.write_uai(m, pu)
+    synth.write_evidence(ev, pe)
+    synth.write_query(q, pq)
+    M = tn.Model.from_uai(pu)
+    E, Q = M.read_evidence(pe), M.read_query(pq)
+    lz, mg = M.mar(E, prec="fp64")
+    for b in range(E.shape[0]):
+        lzr, mr = oracle.brute_mar(m, ev[b])
+        assert abs(lz[b] - lzr) < 1e-10
+        _marg_close(M, mg[b], mr, 1e-10)
+    x, lp = M.map(E[0], prec="fp32")
+    xb, lb = oracle.brute_map(m, ev[0])
+    np.testing.assert_array_equal(x, xb)
+    xq, lq = M.mmap(Q, E[0], prec="fp32")
+    xqb, lqb = oracle.brute_mmap(m, q, ev[0])
+    np.testing.assert_array_equal(xq, xqb)
+    w = synth.workload(3)
+    p3, e3 = str(tmp_path / "bn300.uai"), str(tmp_path / "bn300.uai.evid")
+    synth.write_uai(w.model, p3)
+    synth.write_evidence(w.evid, e3)
+    M3 = tn.Model.from_uai(p3)
+    x3, _ = M3.map(M3.read_evidence(e3)[0], prec="fp32")
+    np.testing.assert_array_equal(x3, oracle.ve_map(w.model, w.evid[0])[0])
+
+
+def test_multi_model_single_launch():
+    """Models of uneven treewidth (grids, a 3-regular graph, a Bayesian
+    network) solved by tn_solve_multi in one graph launch give the FP64
+    results of separate tn_mar calls bit for bit, and the oracle's; PR in
+    TF32 through the same launch within 1e-4."""
+    ms = [synth.grid_ising(10, 31), synth.rrg3_ising(40, 32), synth.bayes_net(60, 33),
+          synth.grid_ising(4, 34)]
+    evs = [synth.evidence_batch(m, k, 0.2, 40 + i) for i, (m, k) in enumerate(zip(ms, [3, 2, 4, 5]))]
+    Ms = [tn.Model.from_synth(m) for m in ms]
+    res = tn.solve_multi(Ms, evs, "mar", "fp64")
+    for M, e, (lz, mg) in zip(Ms, evs, res):
+        lz1, mg1 = M.mar(e, prec="fp64")
+        np.testing.assert_array_equal(lz, lz1)
+        np.testing.assert_array_equal(mg, mg1)
+    for b in range(evs[3].shape[0]):
+        lzr, mr = oracle.brute_mar(ms[3], evs[3][b])
+        assert abs(res[3][0][b] - lzr) < 1e-10
+        _marg_close(Ms[3], res[3][1][b], mr, 1e-10)
+    lzv, mv = oracle.ve_mar(ms[2], evs[2][1])
+    assert abs(res[2][0][1] - lzv) < 1e-10
+    _marg_close(Ms[2], res[2][1][1], mv, 1e-10)
+    res32 = tn.solve_multi(Ms, evs, "pr", "tf32")
+    for (lz, _), (lz64, _) in zip(res32, res):
+        np.testing.assert_allclose(lz, lz64, rtol=1e-4)
+    with pytest.raises(tn.TNError):
+        tn.solve_multi([Ms[0], Ms[0]], [evs[0], evs[0]])
 
 
 def test_workload4_batched_slice():

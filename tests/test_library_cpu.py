@@ -89,6 +89,45 @@ def test_uai_roundtrip_and_parse_errors():
         assert e.value.status == 2
 
 
+def test_uai_evidence_and_query_files():
+    """Evidence files in both UAI forms (one block, or a count of blocks) and
+    MMAP query files read back to the arrays they were written from; malformed
+    files and out-of-range entries are TN_E_PARSE."""
+    m = synth.bayes_net(12, 4)
+    ev = synth.evidence_batch(m, 3, 0.3, 9)
+    q = [7, 2, 10]
+    with tempfile.TemporaryDirectory() as d:
+        pu = os.path.join(d, "m.uai")
+        synth.write_uai(m, pu)
+        M = tn.Model.from_uai(pu)
+        pe = os.path.join(d, "m.uai.evid")
+        synth.write_evidence(ev, pe)
+        np.testing.assert_array_equal(M.read_evidence(pe), ev)
+        # the single-block form
+        obs = np.nonzero(ev[1] >= 0)[0]
+        with open(pe, "w") as f:
+            f.write(" ".join([str(len(obs))] + [f"{v} {ev[1][v]}" for v in obs]))
+        np.testing.assert_array_equal(M.read_evidence(pe), ev[1:2])
+        pq = os.path.join(d, "m.uai.query")
+        synth.write_query(q, pq)
+        np.testing.assert_array_equal(M.read_query(pq), q)
+        for text in ("2 0 1", "1 1 12 0", "1 1 0 5", "1 2 0 1 0 0", "x"):
+            with open(pe, "w") as f:
+                f.write(text)
+            with pytest.raises(tn.TNError) as e:
+                M.read_evidence(pe)
+            assert e.value.status == 2, text
+        for text in ("3 1 2", "2 1 1", "1 40"):
+            with open(pq, "w") as f:
+                f.write(text)
+            with pytest.raises(tn.TNError) as e:
+                M.read_query(pq)
+            assert e.value.status == 2, text
+        with pytest.raises(tn.TNError) as e:
+            M.read_evidence(os.path.join(d, "missing.evid"))
+        assert e.value.status == 1
+
+
 def test_tree_validation():
     m = synth.grid_ising(3, 1)
     M = tn.Model.from_synth(m)

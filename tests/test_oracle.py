@@ -356,3 +356,20 @@ def test_tcon_matches_maxplus_matmul():
     np.testing.assert_array_equal(v2, val)
     for (i, k), (j,) in a2.items():
         assert j == arg[i, k]
+
+
+def test_map_gap_is_the_enumerated_runner_up():
+    """oracle.map_gap: the gap between the MAP assignment and the best other
+    assignment equals the one read off the enumerated joint distribution
+    (log of the top two probabilities), with and without evidence."""
+    for seed in range(3):
+        m = synth.random_markov(9, 12, 3, 50 + seed, cards=(2, 3))
+        ev = np.full(m.nvars, -1, np.int32)
+        if seed:
+            ev[seed] = 1
+        x, lp, gap = oracle.map_gap(m, ev)
+        p = np.sort(oracle.brute_joint(m, ev))[::-1]
+        assert abs(gap - (np.log(p[0]) - np.log(p[1]))) < 1e-9
+        xb, lb = oracle.brute_map(m, ev)
+        np.testing.assert_array_equal(x, xb)
+        assert abs(lp - lb) < 1e-9
