@@ -329,6 +329,11 @@ void bgemm_configure(BDesc &d, int elem_bytes) {
     if ((double)tiles * d.nsplit >= 2147483647.0 || d.M >= (1LL << 31) || d.N >= (1LL << 31) ||
         d.K >= (1LL << 31))
         d.tile = -1;
+    // float data with whole K per tile and wide tiles: the tensor-core gather
+    // kernel (with 32-column tiles its per-tile handoffs cost more than the
+    // CUDA-core multiply-adds; measured on the 3-regular batched workload)
+    d.tc = elem_bytes == 4 && d.tile >= 0 && d.nsplit == 1 && d.N > 64 && d.M >= 128 &&
+           (double)tc_gather_tiles(d) < 2147483647.0;
 }
 
 size_t bgemm_scratch_bytes(const BDesc &d, int elem_bytes) {
@@ -336,12 +341,16 @@ size_t bgemm_scratch_bytes(const BDesc &d, int elem_bytes) {
     return (size_t)d.nsplit * (size_t)(d.G * d.M * d.N * d.nbeta) * (size_t)elem_bytes;
 }
 
-int bgemm_launches(const BDesc &d) { return d.nsplit > 1 ? 2 : 1; }
+int bgemm_launches(const BDesc &d) { return d.nsplit > 1 && !d.tc ? 2 : 1; }
 
 template <typename T>
 void launch_bgemm(const BDesc &d, void *scratch, cudaStream_t st) {
     const int64_t outs = d.G * d.M * d.N * d.nbeta;
     if (outs == 0) return;
+    if (sizeof(T) == 4 && d.tc) {
+        launch_tc_gather(d, st);
+        return;
+    }
     int bm, bn;
     tile_dims<T>(d, bm, bn);
     const int64_t ntiles =

@@ -34,6 +34,8 @@ struct BDesc {
     int nsplit;                    // K split over this many blocks (partials in scratch)
     int64_t kchunk;                // summed indices per split (a multiple of the K tile)
     int tile;                      // tile shape id (see bgemm.cu); -1: does not fit
+    int tc;                        // 1: tensor-core gather kernel (float data, no K split)
+    int *err;                      // set by a bounded device wait that gave up (tc kernel)
 };
 
 // Scratch bytes of the split-K partials (0 when the K space is not split).
@@ -44,5 +46,8 @@ void bgemm_configure(BDesc &d, int elem_bytes);
 template <typename T>
 void launch_bgemm(const BDesc &d, void *scratch, cudaStream_t st);
 int bgemm_launches(const BDesc &d);
+// The tensor-core form (tcgather.cu): tiles of 128 rows, and its launch.
+int64_t tc_gather_tiles(const BDesc &d);
+void launch_tc_gather(const BDesc &d, cudaStream_t st);
 
 }  // namespace tn

@@ -911,7 +911,18 @@ static bool make_bgemm(const std::vector<int> &card, const Labels &lx, bool bx, 
     d.M = prod(M);
     d.N = prod(N);
     d.K = prod(K);
-    if (!swapped && d.N > d.M)
+    // orientation: for float data (tensor-core gather kernel, whose epilogue
+    // stores along M) put the output's fastest label on the M side, else the
+    // larger side on M
+    auto fastest_of = [&](const Labels &lt) {
+        for (int k = (int)lt.size() - 1; k >= 0; --k)
+            if (card[lt[k]] > 1) return lt[k];
+        return -1;
+    };
+    const int fo = fastest_of(lo);
+    const bool o_in_n = std::find(N.begin(), N.end(), fo) != N.end();
+    const bool o_in_m = std::find(M.begin(), M.end(), fo) != M.end();
+    if (!swapped && (esz == 4 ? (o_in_n || (!o_in_m && d.N > d.M)) : d.N > d.M))
         return make_bgemm(card, ly, by, pery, Y, mxy, lx, bx, perx, X, mxx, lo, bo, pero, O, mxo,
                           nbeta, esz, d, tab, true);
     if (perx >= (1LL << 31) || pery >= (1LL << 31) || pero >= (1LL << 31)) return false;
@@ -1773,8 +1784,18 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
         }
     }
     for (auto *steps : {&P.fsteps, &P.bsteps})
-        for (auto &st : *steps)
+        for (auto &st : *steps) {
             if (st.kind == 2) st.ad.bps = P.tune.absorb_bps;
+            if (st.kind == 4) {
+                st.bd.err = m->d_err;
+                // programs keep the FP32 CUDA-core form: in the evidence-
+                // batched tree the persistent tensor-core gather kernel (one
+                // CTA per SM) measured slower (it holds every SM against the
+                // other lanes of the graph) and its TF32 inputs raised the
+                // log Z error; tn_contract_dev uses it for TF32 / BF16
+                st.bd.tc = 0;
+            }
+        }
     trace_program(P);
     // inner offset tables of the streaming steps, one device buffer
     {
@@ -3426,6 +3447,23 @@ tn_status tn_mmap(tn_model *m, const int32_t *evid, int nq, const int32_t *query
 }
 
 // One pairwise contraction on caller-provided device buffers.
+// One wait-timeout flag per device for the single-contraction entry points,
+// created on first use.
+static tn_status device_err_flag(int **out) {
+    static std::mutex err_mu;
+    static std::map<int, int *> err_flags;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(err_mu);
+    int *&f = err_flags[dev];
+    if (!f) {
+        CK(cudaMalloc(&f, 16));
+        CK(cudaMemset(f, 0, 16));
+    }
+    *out = f;
+    return TN_OK;
+}
+
 tn_status tn_contract_dev(int nlabels, const int *sizes, int na, const int *labels_a,
                           const void *A, int nb, const int *labels_b, const void *B, int nc,
                           const int *labels_c, void *C, int semiring, int dtype, tn_prec prec,
@@ -3512,20 +3550,10 @@ tn_status tn_contract_dev(int nlabels, const int *sizes, int na, const int *labe
                 op.post.in = wd;
             }
             bool tc = (prec == TN_TF32 || prec == TN_BF16) && dtype == 1 && tc_gemm_supported(op.g);
-            // one wait-timeout flag per device, created on first use
-            static std::mutex err_mu;
-            static std::map<int, int *> err_flags;
             int *d_err = nullptr;
             {
-                int dev = 0;
-                CK(cudaGetDevice(&dev));
-                std::lock_guard<std::mutex> lk(err_mu);
-                int *&f = err_flags[dev];
-                if (!f) {
-                    CK(cudaMalloc(&f, 16));
-                    CK(cudaMemset(f, 0, 16));
-                }
-                d_err = f;
+                tn_status fs = device_err_flag(&d_err);
+                if (fs) return fs;
             }
             launch_permute(op.px, st);
             launch_permute(op.py, st);
@@ -3572,6 +3600,9 @@ tn_status tn_contract_dev(int nlabels, const int *sizes, int na, const int *labe
                                       &bd.tcn, &bd.tak, &bd.tbk})
                 *q = dtab + (intptr_t)*q;
             if (pb) CK(cudaMallocAsync(&part, pb, st));
+            tn_status fs = device_err_flag(&bd.err);
+            if (fs) return fs;
+            if (!(prec == TN_TF32 || prec == TN_BF16)) bd.tc = 0;   // TF32 inputs only when asked
             if (dtype == 0) launch_bgemm<double>(bd, part, st);
             else launch_bgemm<float>(bd, part, st);
             cudaError_t e = cudaGetLastError();
@@ -3583,6 +3614,12 @@ tn_status tn_contract_dev(int nlabels, const int *sizes, int na, const int *labe
                 return fail(TN_E_CUDA, std::string("batched GEMM launch: ") +
                                            cudaGetErrorString(e != cudaSuccess ? e : e2));
             CK(cudaStreamSynchronize(st));
+            int herr = 0;
+            CK(cudaMemcpy(&herr, bd.err, 4, cudaMemcpyDeviceToHost));
+            if (herr) {
+                CK(cudaMemset(bd.err, 0, 4));
+                return fail(TN_E_TIMEOUT, "a device-side wait exceeded its time limit");
+            }
             return TN_OK;
         }
     }

@@ -352,6 +352,43 @@ def test_gemm_form_matches_definition(case, prec):
         assert err <= GEMM_TOL[prec], (prec, err)
 
 
+# shapes of the batched strided GEMM (groups G, M, N, K in scattered layouts)
+# for its tensor-core gather form: sizes, labels A, labels B, labels C
+GATHER_CASES = [
+    ([300, 37, 70], [0, 1], [1, 2], [0, 2]),                       # A summed-fastest
+    ([3, 50, 9, 20, 6], [1, 0, 3], [3, 2, 0, 4], [2, 1, 4, 0]),    # G label fastest in C
+    ([4, 100, 30], [0, 1], [1, 2], [0, 2]),                        # roles swapped
+    ([2] * 18, list(range(13)) + [13, 14], [13, 14, 15, 16, 17],   # M = 2^13, K = 4, N = 8
+     list(range(13)) + [15, 16, 17]),
+    ([512, 40, 300, 2], [3, 0, 1], [3, 1, 2], [3, 2, 0]),          # N = 300: two 256-wide tiles
+    ([2] * 20, list(range(20)), [5, 12], [5, 12]),                 # M = N = 2, K = 2^18
+    ([1000, 64, 48], [1, 0], [2, 1], [0, 2]),                      # A rows strided by 64
+    # M = 4096, K = 8, N = 128 with the output's fastest label on the N side
+    ([2] * 22, list(range(15)), list(range(12, 22)), list(range(12)) + list(range(15, 22))),
+]
+
+
+@pytest.mark.parametrize("case", range(len(GATHER_CASES)))
+def test_gather_gemm_tf32_matches_definition(case):
+    """The batched strided GEMM with TF32 inputs (the tensor-core gather form
+    where it applies, else the CUDA-core form) against the definition, twice
+    in a row (shared-memory ring and TMEM reused cleanly)."""
+    sizes, la, lb, lc = GATHER_CASES[case]
+    rng = np.random.default_rng(300 + case)
+    A = rng.random([sizes[v] for v in la])
+    B = rng.random([sizes[v] for v in lb])
+    ref = np.einsum(A, la, B, lb, lc)
+    tA = torch.tensor(A, dtype=torch.float32, device="cuda")
+    tB = torch.tensor(B, dtype=torch.float32, device="cuda")
+    tC = torch.zeros([sizes[v] for v in lc], dtype=torch.float32, device="cuda")
+    for _ in range(2):
+        tC.fill_(float("nan"))
+        tn.contract_dev(sizes, la, tA, lb, tB, lc, tC, prec="tf32")
+        got = tC.cpu().numpy()
+        err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+        assert err <= 2e-3, (case, err)
+
+
 def test_autograd_factor_marginals():
     """d log Z / d log T_f[x] is the factor marginal: a unary factor's equals
     the oracle's variable marginal, each sums to one, and finite differences
