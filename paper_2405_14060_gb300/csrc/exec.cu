@@ -882,7 +882,8 @@ static bool make_bgemm(const std::vector<int> &card, const Labels &lx, bool bx, 
                        int64_t pery, const void *Y, const unsigned long long *mxy,
                        const Labels &lo, bool bo, int64_t pero, void *O,
                        unsigned long long *mxo, int nbeta, int esz, BDesc &d,
-                       std::vector<int32_t> &tab, bool swapped = false) {
+                       std::vector<int32_t> &tab, bool tc_orient = false,
+                       bool swapped = false) {
     std::memset(&d, 0, sizeof d);
     if (bo != (bx || by)) return false;
     std::set<int> sx(lx.begin(), lx.end()), sy(ly.begin(), ly.end()), so(lo.begin(), lo.end());
@@ -911,9 +912,9 @@ static bool make_bgemm(const std::vector<int> &card, const Labels &lx, bool bx, 
     d.M = prod(M);
     d.N = prod(N);
     d.K = prod(K);
-    // orientation: for float data (tensor-core gather kernel, whose epilogue
-    // stores along M) put the output's fastest label on the M side, else the
-    // larger side on M
+    // orientation: for the tensor-core gather kernel (float data, epilogue
+    // storing along M) the output's fastest label on the M side; for the
+    // CUDA-core kernel the larger side on M
     auto fastest_of = [&](const Labels &lt) {
         for (int k = (int)lt.size() - 1; k >= 0; --k)
             if (card[lt[k]] > 1) return lt[k];
@@ -922,9 +923,9 @@ static bool make_bgemm(const std::vector<int> &card, const Labels &lx, bool bx, 
     const int fo = fastest_of(lo);
     const bool o_in_n = std::find(N.begin(), N.end(), fo) != N.end();
     const bool o_in_m = std::find(M.begin(), M.end(), fo) != M.end();
-    if (!swapped && (esz == 4 ? (o_in_n || (!o_in_m && d.N > d.M)) : d.N > d.M))
+    if (!swapped && (tc_orient && esz == 4 ? (o_in_n || (!o_in_m && d.N > d.M)) : d.N > d.M))
         return make_bgemm(card, ly, by, pery, Y, mxy, lx, bx, perx, X, mxx, lo, bo, pero, O, mxo,
-                          nbeta, esz, d, tab, true);
+                          nbeta, esz, d, tab, tc_orient, true);
     if (perx >= (1LL << 31) || pery >= (1LL << 31) || pero >= (1LL << 31)) return false;
     const int64_t ntab = 3 * d.G + 2 * d.M + 2 * d.N + 2 * d.K;
     if (ntab > (1LL << 26)) return false;
@@ -3589,8 +3590,9 @@ tn_status tn_contract_dev(int nlabels, const int *sizes, int na, const int *labe
     if (semiring == 0) {
         BDesc bd;
         std::vector<int32_t> tab;
+        const bool tc_in = prec == TN_TF32 || prec == TN_BF16;
         if (make_bgemm(card, la, false, 0, A, nullptr, lb, false, 0, B, nullptr, lc, false, 0, C,
-                       nullptr, 1, es, bd, tab)) {
+                       nullptr, 1, es, bd, tab, tc_in)) {
             int32_t *dtab = nullptr;
             void *part = nullptr;
             size_t pb = bgemm_scratch_bytes(bd, es);
@@ -3602,7 +3604,7 @@ tn_status tn_contract_dev(int nlabels, const int *sizes, int na, const int *labe
             if (pb) CK(cudaMallocAsync(&part, pb, st));
             tn_status fs = device_err_flag(&bd.err);
             if (fs) return fs;
-            if (!(prec == TN_TF32 || prec == TN_BF16)) bd.tc = 0;   // TF32 inputs only when asked
+            if (!tc_in) bd.tc = 0;   // TF32 inputs only when asked
             if (dtype == 0) launch_bgemm<double>(bd, part, st);
             else launch_bgemm<float>(bd, part, st);
             cudaError_t e = cudaGetLastError();
