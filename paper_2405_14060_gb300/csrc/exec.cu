@@ -1810,6 +1810,7 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                     for (auto pr : {std::make_pair(&g.px, &g.tpx), std::make_pair(&g.py, &g.tpy),
                                     std::make_pair(&g.post, &g.tpost)}) {
                         if (pr.first->tl.tn <= 0) continue;
+                        all.resize((all.size() + 3) & ~(size_t)3);   // 16-byte aligned
                         pwhere.push_back({pr.first, all.size()});
                         all.insert(all.end(), pr.second->begin(), pr.second->end());
                     }
@@ -3532,6 +3533,7 @@ tn_status tn_contract_dev(int nlabels, const int *sizes, int na, const int *labe
             for (auto pr : {std::make_pair(&op.px, &op.tpx), std::make_pair(&op.py, &op.tpy),
                             std::make_pair(&op.post, &op.tpost)}) {
                 if (pr.first->tl.tn <= 0) continue;
+                tall.resize((tall.size() + 3) & ~(size_t)3);   // 16-byte aligned
                 pr.first->tl.ttab = (const int32_t *)(uintptr_t)tall.size();   // offset for now
                 tall.insert(tall.end(), pr.second->begin(), pr.second->end());
             }

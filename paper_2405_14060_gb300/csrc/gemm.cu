@@ -104,31 +104,33 @@ __device__ __forceinline__ void store_conv(void *out, int64_t i, TI x) {
 }
 
 // Tiled form: each block walks a contiguous range of tiles (up to PT_MAXN
-// entries each, input and output runs of at least 32 entries) with two
-// shared-memory buffers: the asynchronous copies of the next tile's input are
-// in flight while the current tile is written out.  One thread advances the
-// tile's base offsets digit by digit and publishes them in shared memory.
-// Loads follow the input order (t.vin inputs per 16-byte copy when the plan
-// allows), stores the output order (t.vec outputs per 16-byte store).
-// Shared slots: input-order entry e sits at e + 4 (e / 32), which keeps
-// 16-byte groups aligned and spreads column reads over the banks.
+// entries each, input and output runs of at least 32 entries) through three
+// shared-memory buffers: while tile q is written out, the asynchronous copies
+// of tiles q + 1 and q + 2 are in flight, and one barrier per tile both
+// publishes a landed tile and frees the buffer of the previous one.  Thread 0
+// advances the tiles' base offsets digit by digit, three tiles ahead, and
+// publishes them in shared memory.  Loads follow the input order (t.vin
+// inputs per 16-byte copy when the plan allows), stores the output order
+// (t.vec outputs per 16-byte store, their shared-memory slots read as one
+// vector of 16-bit integers).
 template <typename TI, int OT>
 __global__ void __launch_bounds__(256) k_permute_tiled(const __grid_constant__ PDesc p,
                                                        int64_t per_item) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ int64_t sbase[3][3];   // per tile (mod 3): input base, output base, item
+    __shared__ int64_t sbase[4][3];   // per tile (mod 4): input base, output base, item
     const PTile &t = p.tl;
     const int n = t.tn;
-    const int nbuf = n + 4 * (n >> 5) + 4;
+    const int nbuf = t.nbuf, swz = t.swz;
     TI *sm0 = (TI *)smraw;
     const int64_t item = blockIdx.y;
-    const int32_t *tin = t.ttab, *tout = t.ttab + n, *slot = t.ttab + 2 * n;
+    const int32_t *tin = t.ttab, *tout = t.ttab + n;
+    const uint16_t *slot = (const uint16_t *)(t.ttab + 2 * n);
     const TI *in = (const TI *)p.in;
     TI mxv = 0;
     // this block's tiles [q0, q1)
     const int64_t q0 = per_item * blockIdx.x / gridDim.x;
     const int64_t q1 = per_item * (blockIdx.x + 1) / gridDim.x;
-    // digits of the current tile (thread 0 only)
+    // digits of the last published tile (thread 0 only)
     int32_t dg[MAXD];
     int64_t cbi = 0, cbo = 0;
     if (threadIdx.x == 0) {
@@ -147,7 +149,7 @@ __global__ void __launch_bounds__(256) k_permute_tiled(const __grid_constant__ P
             cbo += (int64_t)v * t.rout[k];
         }
     }
-    // thread 0: publish the bases of tile q (q0, q0 + 1, ... in order)
+    // thread 0: publish the bases of tile q (called for q0, q0 + 1, ... in order)
     auto publish = [&](int64_t q) {
         if (threadIdx.x != 0 || q >= q1) return;
         if (q > q0) {
@@ -160,27 +162,28 @@ __global__ void __launch_bounds__(256) k_permute_tiled(const __grid_constant__ P
                 dg[k] = 0;
             }
         }
-        const int s = (int)(q % 3);
+        const int s = (int)(q & 3);
         sbase[s][0] = cbi;
         sbase[s][1] = cbo;
         sbase[s][2] = t.rest_beta >= 0 ? dg[t.rest_beta] : 0;
     };
     const bool vin = t.vin > 0 && ((uintptr_t)p.in & 15) == 0;
+    // copies of tile q into buffer buf (an empty group past the range)
     auto issue = [&](int64_t q, int buf) {
         if (q < q1) {
-            const int64_t bi = sbase[q % 3][0];
+            const int64_t bi = sbase[q & 3][0];
             const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(sm0 + buf * nbuf);
             if (vin) {
                 constexpr int GI = 16 / (int)sizeof(TI);
                 for (int e = threadIdx.x * GI; e < n; e += 256 * GI)
                     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
-                                     s0 + (uint32_t)((e + 4 * (e >> 5)) * sizeof(TI))),
+                                     s0 + (uint32_t)(pt_slot<sizeof(TI)>(e, swz) * sizeof(TI))),
                                  "l"(in + bi + __ldg(tin + e))
                                  : "memory");
             } else {
                 for (int e = threadIdx.x; e < n; e += 256)
                     asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(
-                                     s0 + (uint32_t)((e + 4 * (e >> 5)) * sizeof(TI))),
+                                     s0 + (uint32_t)(pt_slot<sizeof(TI)>(e, swz) * sizeof(TI))),
                                  "l"(in + bi + __ldg(tin + e)), "n"(sizeof(TI))
                                  : "memory");
             }
@@ -189,25 +192,33 @@ __global__ void __launch_bounds__(256) k_permute_tiled(const __grid_constant__ P
     };
     const bool vec = t.vec > 0 && ((uintptr_t)p.out & 15) == 0;
     publish(q0);
+    publish(q0 + 1);
+    publish(q0 + 2);
     __syncthreads();
     issue(q0, 0);
+    issue(q0 + 1, 1);
     int buf = 0;
     for (int64_t q = q0; q < q1; ++q) {
-        publish(q + 1);
-        __syncthreads();          // bases of q + 1 visible; buffer buf ^ 1 free
-        issue(q + 1, buf ^ 1);
         cp_async_wait<1>();
-        __syncthreads();          // tile q landed
-        const int64_t bo = sbase[q % 3][1], beta = sbase[q % 3][2];
+        // every thread's copies of tile q landed, every thread is done with
+        // tile q - 1 (its buffer is free), and the bases of q + 2 are visible
+        __syncthreads();
+        issue(q + 2, buf == 0 ? 2 : buf - 1);
+        publish(q + 3);
+        const int64_t bo = sbase[q & 3][1], beta = sbase[q & 3][2];
         const TI sc = p.mxi ? pow2neg<TI>(exp_of_bits(p.mxi[beta * p.mxi_bs])) : TI(1);
         const TI *sm = sm0 + buf * nbuf;
         if (vec) {
             constexpr int G = OT == E_F64 ? 2 : OT == E_F32 ? 4 : 8;
             for (int e0 = threadIdx.x * G; e0 < n; e0 += 256 * G) {
+                uint16_t sl[G];
+                if (G == 8) *(uint4 *)sl = __ldg((const uint4 *)(slot + e0));
+                else if (G == 4) *(uint2 *)sl = __ldg((const uint2 *)(slot + e0));
+                else *(uint32_t *)sl = __ldg((const uint32_t *)(slot + e0));
                 TI x[G];
 #pragma unroll
                 for (int j = 0; j < G; ++j) {
-                    x[j] = sm[__ldg(slot + e0 + j)] * sc;
+                    x[j] = sm[sl[j]] * sc;
                     mxv = mxv > x[j] ? mxv : x[j];
                 }
                 const int64_t o = bo + __ldg(tout + e0);
@@ -234,7 +245,7 @@ __global__ void __launch_bounds__(256) k_permute_tiled(const __grid_constant__ P
                 mxv = mxv > x ? mxv : x;
             }
         }
-        buf ^= 1;
+        buf = buf == 2 ? 0 : buf + 1;
     }
     cp_async_wait<0>();
     if (p.mxo) block_max_atomic(p.mxo + item, (double)mxv);
@@ -305,7 +316,8 @@ void plan_permute_tiles(PDesc &p, std::vector<int32_t> &tab) {
             w *= d[i].sz;
         }
     }
-    tab.assign((size_t)3 * n, 0);
+    // input offsets [n], output offsets [n], then the 16-bit slots [n]
+    tab.assign((size_t)(2 * n + (n + 1) / 2), 0);
     for (int64_t e = 0; e < n; ++e) {
         int64_t r = e, off = 0;
         for (int i : oi) {
@@ -319,6 +331,7 @@ void plan_permute_tiles(PDesc &p, std::vector<int32_t> &tab) {
         }
         tab[e] = (int32_t)off;
     }
+    std::vector<int> ein_of((size_t)n);
     for (int64_t e = 0; e < n; ++e) {
         int64_t r = e, off = 0, ein = 0;
         for (int i : oo) {
@@ -332,7 +345,7 @@ void plan_permute_tiles(PDesc &p, std::vector<int32_t> &tab) {
             return;
         }
         tab[n + e] = (int32_t)off;
-        tab[2 * n + e] = (int32_t)(ein + 4 * (ein >> 5));
+        ein_of[e] = (int)ein;
     }
     PTile &t = p.tl;
     t.nrest = 0;
@@ -386,6 +399,47 @@ void plan_permute_tiles(PDesc &p, std::vector<int32_t> &tab) {
         for (int k = 0; ok && k < t.nrest; ++k) ok = t.rin[k] % G == 0;
         if (ok) t.vin = G;
     }
+    // shared-memory layout: the one whose reads of a tile (output order,
+    // t.vec entries per thread, or one) take the fewest wavefronts
+    {
+        const int esz = p.in_type == E_F64 ? 8 : 4;
+        const int G = t.vec > 0 ? t.vec : 1;
+        auto slot_of = [&](int e, int swz) {
+            return esz == 8 ? pt_slot<8>(e, swz) : pt_slot<4>(e, swz);
+        };
+        int64_t best = -1;
+        std::vector<int> sl((size_t)n);
+        for (int swz = 0; swz < PT_NSWZ; ++swz) {
+            for (int64_t e = 0; e < n; ++e) sl[e] = slot_of(ein_of[e], swz);
+            int64_t waves = 0;
+            for (int64_t b = 0; b < n; b += 256 * G)
+                for (int w = 0; w < 8; ++w)
+                    for (int j = 0; j < G; ++j) {
+                        // one warp-wide shared load: per bank, the distinct words
+                        int cnt[32] = {0};
+                        int64_t seen[32][32];
+                        for (int l = 0; l < 32; ++l) {
+                            const int64_t e = b + (int64_t)(w * 32 + l) * G + j;
+                            if (e >= n) continue;
+                            const int64_t word = (int64_t)sl[e] * (esz / 4);
+                            const int bank = (int)(word & 31);
+                            bool dup = false;
+                            for (int k = 0; k < cnt[bank]; ++k) dup = dup || seen[bank][k] == word;
+                            if (!dup) seen[bank][cnt[bank]++] = word;
+                        }
+                        int mx = 0;
+                        for (int k = 0; k < 32; ++k) mx = std::max(mx, cnt[k]);
+                        waves += mx;
+                    }
+            if (best < 0 || waves < best) {
+                best = waves;
+                t.swz = swz;
+            }
+        }
+        t.nbuf = pt_nbuf((int)n, t.swz);
+        uint16_t *s16 = (uint16_t *)(tab.data() + 2 * n);
+        for (int64_t e = 0; e < n; ++e) s16[e] = (uint16_t)slot_of(ein_of[e], t.swz);
+    }
 }
 
 void launch_permute(const PDesc &p, cudaStream_t st) {
@@ -393,13 +447,14 @@ void launch_permute(const PDesc &p, cudaStream_t st) {
     if (p.tl.tn > 0 && p.tl.ttab) {
         int nitems = (p.mxo && p.tl.rest_beta == 0) ? p.tl.rsz[0] : 1;
         int64_t per = p.tl.ntiles / nitems;
-        int64_t cap = std::max<int64_t>(1, (152LL * 6) / nitems);
+        // three tile buffers; as many blocks per SM as shared memory holds
+        size_t sm = 3 * (size_t)p.tl.nbuf * (p.in_type == E_F64 ? 8 : 4);
+        const int64_t bps = std::max<int64_t>(1, std::min<int64_t>(8, (227 * 1024) / (sm + 1024)));
+        int64_t cap = std::max<int64_t>(1, (152LL * bps) / nitems);
         dim3 grid((unsigned)std::max<int64_t>(1, std::min(per, cap)), (unsigned)nitems, 1);
-        // two tile buffers
-        size_t sm = 2 * (size_t)(p.tl.tn + 4 * (p.tl.tn / 32) + 4) * (p.in_type == E_F64 ? 8 : 4);
         static std::once_flag once;
         std::call_once(once, [] {
-            const int mx = 2 * (PT_MAXN + 4 * (PT_MAXN / 32) + 4) * 8;
+            const int mx = 3 * pt_nbuf(PT_MAXN, 0) * 8;
             cudaFuncSetAttribute(k_permute_tiled<double, E_F64>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
             cudaFuncSetAttribute(k_permute_tiled<float, E_F32>,

@@ -23,12 +23,37 @@ enum ElemType { E_F64 = 0, E_F32 = 1, E_BF16 = 2 };
 // whose input or output stride is below 32 elements goes into one tile of
 // tn <= 4096 entries staged in shared memory, so that loads run along the
 // input's contiguous runs and stores along the output's; the other dims
-// enumerate the tiles.  Device table ttab: input offsets [tn] (input order),
-// output offsets [tn] (output order), and for each output-order entry its
-// padded shared-memory slot [tn].
+// enumerate the tiles.  Device table ttab (16-byte aligned): input offsets
+// [tn] (input order), output offsets [tn] (output order), and for each
+// output-order entry its shared-memory slot as 16-bit integers [tn].  The
+// slot of input-order entry e follows the layout `swz` (pt_slot), chosen on
+// the host as the one with the fewest shared-memory wavefronts for the
+// tile's read pattern.
 constexpr int PT_MAXN = 4096;
+
+// Shared-memory slot of input-order tile entry e: layout 0 pads every run of
+// 32 entries by 4; layouts 1-3 permute the 16-byte groups inside each run of
+// 32 entries by an XOR with a hash of the run index.  All keep 16-byte
+// groups whole, so 16-byte asynchronous copies stay aligned.
+constexpr int PT_NSWZ = 4;
+template <int ESZ>
+__host__ __device__ __forceinline__ int pt_slot(int e, int swz) {
+    constexpr int GI = 16 / ESZ;   // entries per 16-byte group
+    if (swz == 0) return e + 4 * (e >> 5);
+    const int r = e >> 5, w = e & 31;
+    const int h = (swz == 1 ? r ^ (r >> 3) : swz == 2 ? r ^ ((r >> 3) << 1) : r) & 7;
+    return (r << 5) + ((w / GI) ^ h) * GI + (w % GI);
+}
+
+// Shared-memory entries of one tile buffer of n entries in layout swz.
+__host__ __device__ __forceinline__ int pt_nbuf(int n, int swz) {
+    return swz == 0 ? n + 4 * (n >> 5) + 4 : (n + 31) & ~31;
+}
+
 struct PTile {
     int tn;                          // 0: not tiled
+    int swz;                         // shared-memory layout of a tile (pt_slot)
+    int nbuf;                        // shared-memory entries per tile buffer
     int nrest, rest_beta;            // rest dims, index of the batch dim among them (-1)
     int32_t rsz[MAXD], rsh[MAXD];    // rest sizes, log2 (-1: not a power of two)
     int64_t rin[MAXD], rout[MAXD];
