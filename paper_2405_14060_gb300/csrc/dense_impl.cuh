@@ -1,0 +1,457 @@
+// Dense streaming contractions for nodes with many summed x new combinations
+// (more than the register-blocked absorb and reduce kernels take, up to
+// 32 x 32): a big tensor against a small dense block, the shape that binary
+// labels give when five labels are summed and five are new, and the
+// adjoint steps of such nodes (Thm. "Tensor network differentiation",
+// Eq. einback).  Both read every entry of the big operands from HBM once.
+//
+//   k_absorb_dense   Y[t, r] = sum_s X[r, s] W[s, t]: W staged once per block
+//                    in shared memory as [s][t]; tiles of 128 positions r of X
+//                    staged by asynchronous copies two tiles ahead (as [s][p]
+//                    when positions are contiguous in X, as [p][s] when the
+//                    summed combinations are); each thread owns 4 positions x
+//                    4 new combinations and reads 16-byte vectors of both.
+//   k_reduce_dense   O[g, s, t] = sum_m X[g, m, s] Z[g, m, t]: tiles of 64
+//                    positions of both operands staged as [p][s | t]; four
+//                    thread groups take a quarter of each tile's positions,
+//                    each thread 4 x 4 outputs of the 32 x 32 block; per-block
+//                    partials summed by the group's last block in a fixed order
+//                    (deterministic).
+#pragma once
+#include <algorithm>
+#include <cstdint>
+#include <mutex>
+
+#include "devutil.cuh"
+#include "stream.cuh"
+
+namespace tn {
+
+// Group offsets of a reduce descriptor's group index gi in X, Z and O.
+__device__ __forceinline__ void group_offsets(const RDesc &d, int64_t gi, int64_t &ox,
+                                              int64_t &oz, int64_t &oo) {
+    for (int i = d.ngd - 1; i >= 0; --i) {
+        int64_t dg = gi % d.gsz[i];
+        gi /= d.gsz[i];
+        ox += dg * d.gsx[i];
+        oz += dg * d.gsz2[i];
+        oo += dg * d.gso[i];
+    }
+}
+
+// Outer decode of the summed positions: operand offsets of outer index o.
+__device__ __forceinline__ void reduce_outer(const RDesc &d, int64_t o, int nod, int64_t &cbx,
+                                             int64_t &cbz) {
+    if (d.pow2m) {
+        const int64_t r0 = o * d.nin;
+        for (int q = 0; q < nod; ++q) {
+            int64_t dg = (r0 >> d.msh[q]) & (int64_t)(d.msz[q] - 1);
+            cbx += dg * d.msx[q];
+            cbz += dg * d.msz2[q];
+        }
+    } else {
+        int64_t r = o;
+        for (int q = nod - 1; q >= 0; --q) {
+            int64_t dg = r % d.msz[q];
+            r /= d.msz[q];
+            cbx += dg * d.msx[q];
+            cbz += dg * d.msz2[q];
+        }
+    }
+}
+
+// Four consecutive entries as 16-byte vectors (one float4, two double2).
+__device__ __forceinline__ void ld4(const float *p, float (&v)[4]) {
+    const float4 a = *(const float4 *)p;
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = a.z;
+    v[3] = a.w;
+}
+__device__ __forceinline__ void ld4(const double *p, double (&v)[4]) {
+    const double2 a = *(const double2 *)p, b = *(const double2 *)(p + 2);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float *p, float a, float b, float c, float d) {
+    *(float4 *)p = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void st4(double *p, double a, double b, double c, double d) {
+    *(double2 *)p = make_double2(a, b);
+    *(double2 *)(p + 2) = make_double2(c, d);
+}
+// Asynchronous copy of four consecutive entries (16 bytes per instruction),
+// zeros instead when !ok.
+template <typename T>
+__device__ __forceinline__ void cp_async4(uint32_t s, const T *g, bool ok) {
+#pragma unroll
+    for (int h = 0; h < (int)sizeof(T) / 4; ++h)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s + 16 * h),
+                     "l"(g + h * (16 / (int)sizeof(T))), "r"(ok ? 16 : 0)
+                     : "memory");
+}
+// One entry, zeros instead when !ok.
+template <typename T>
+__device__ __forceinline__ void cp_async1(uint32_t s, const T *g, bool ok) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(s), "l"(g),
+                 "n"(sizeof(T)), "r"(ok ? (int)sizeof(T) : 0)
+                 : "memory");
+}
+
+// Launch modes of the dense absorb, chosen on the host from the descriptor:
+// X: 0 one entry per copy into [s][p], 1 four positions per copy into
+// [s][p], 2 four summed combinations per copy into [p][s];
+// Y: 0 one entry per store, 1 four positions per store, 2 four new
+// combinations per store.
+struct DenseModes {
+    int xm, ym;
+};
+
+constexpr int AD_P = 128;   // positions per tile
+constexpr int AD_S = 3;     // tile buffers
+
+template <typename T>
+__host__ __device__ constexpr int ad_pad() {
+    return 16 / (int)sizeof(T);
+}
+template <typename T>
+__host__ __device__ constexpr size_t absorb_dense_smem() {
+    // W [32][32 + pad], tiles [AD_S][32 x (AD_P + pad)] (either layout fits)
+    return ((size_t)32 * (32 + ad_pad<T>()) +
+            (size_t)AD_S * std::max(32 * (AD_P + ad_pad<T>()), AD_P * (32 + ad_pad<T>()))) *
+           sizeof(T);
+}
+
+// Outer decode of position tile o (outer index): operand bases.
+__device__ __forceinline__ void absorb_outer(const ADesc &d, int64_t o, int nod, int64_t &bx,
+                                             int64_t &by) {
+    if (d.pow2r) {
+        const int64_t r0 = o * d.nin;
+        for (int k = 0; k < nod; ++k) {
+            const int64_t dg = (r0 >> d.rsh[k]) & (int64_t)(d.rsz[k] - 1);
+            bx += dg * d.rsx[k];
+            by += dg * d.rsy[k];
+        }
+    } else {
+        int64_t r = o;
+        for (int k = nod - 1; k >= 0; --k) {
+            const int64_t dg = r % d.rsz[k];
+            r /= d.rsz[k];
+            bx += dg * d.rsx[k];
+            by += dg * d.rsy[k];
+        }
+    }
+}
+
+template <typename T, int XM>
+__global__ void __launch_bounds__(256) k_absorb_dense(const __grid_constant__ ADesc d, int ym) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    constexpr int PAD = ad_pad<T>();
+    constexpr int WR = 32 + PAD;                                  // W row: [s][t]
+    constexpr int RS = XM == 2 ? 32 + PAD : AD_P + PAD;           // tile row
+    constexpr int TB = XM == 2 ? AD_P * RS : 32 * RS;             // tile buffer
+    T *Ws = (T *)smraw;
+    T *Xs = Ws + 32 * WR;
+    const int tid = threadIdx.x;
+    const int nin = (int)d.nin;
+    const int *tx = d.tab, *ty = d.tab + nin;
+    const int nod = d.nrd - d.nin_d;
+    const int64_t beta = blockIdx.y;
+    const int ns4 = (d.ns + 3) & ~3;
+    {
+        const T *Wg = (const T *)d.W + beta * d.bsw;
+        for (int i = tid; i < 32 * 32; i += 256) {
+            const int s = i >> 5, t = i & 31;
+            Ws[s * WR + t] = (s < d.ns && t < d.nt) ? __ldg(Wg + d.wso[s] + d.wto[t]) : T(0);
+        }
+    }
+    const T sx = d.mxx ? pow2neg<T>(exp_of_bits(d.mxx[beta * d.mxx_bs])) : T(1);
+    const T sw = d.mxw ? pow2neg<T>(exp_of_bits(d.mxw[beta * d.mxw_bs])) : T(1);
+    const T scale = sx * sw;
+    const int nch = (nin + AD_P - 1) / AD_P;
+    const int64_t ntile = d.nouter * nch;
+    const int lnch = log2_if_pow2(nch);
+    const int64_t mine =
+        ntile > blockIdx.x ? (ntile - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    const T *X = (const T *)d.X + beta * d.bsx;
+    T *Y = (T *)d.Y + beta * d.bsy;
+    const uint32_t xs0 = (uint32_t)__cvta_generic_to_shared(Xs);
+    // copies of this block's k-th tile into buffer b (an empty group past the end)
+    auto issue = [&](int64_t k, int b) {
+        if (k < mine) {
+            int64_t crem;
+            const int64_t o = div_tile((int64_t)blockIdx.x + k * gridDim.x, nch, lnch, crem);
+            int64_t bx = 0, by = 0;
+            absorb_outer(d, o, nod, bx, by);
+            const int j0 = (int)crem * AD_P;
+            const T *Xo = X + bx;
+            const uint32_t sb = xs0 + (uint32_t)(b * TB * sizeof(T));
+            if (XM == 1) {
+                // 32 rows x 32 quads of positions
+                for (int e = tid; e < 32 * (AD_P / 4); e += 256) {
+                    const int s = e / (AD_P / 4), p = (e % (AD_P / 4)) * 4;
+                    const int j = j0 + p;
+                    const bool ok = s < d.ns && j < nin;
+                    cp_async4<T>(sb + (uint32_t)((s * RS + p) * sizeof(T)),
+                                 ok ? Xo + __ldg(tx + j) + d.xoff[s] : Xo, ok);
+                }
+            } else if (XM == 2) {
+                // AD_P rows x (ns / 4) quads of summed combinations
+                for (int e = tid; e < AD_P * 8; e += 256) {
+                    const int p = e >> 3, s = (e & 7) * 4;
+                    const int j = j0 + p;
+                    const bool ok = s < d.ns && j < nin;
+                    cp_async4<T>(sb + (uint32_t)((p * RS + s) * sizeof(T)),
+                                 ok ? Xo + __ldg(tx + j) + d.xoff[s] : Xo, ok);
+                }
+            } else {
+                for (int e = tid; e < 32 * AD_P; e += 256) {
+                    const int s = e / AD_P, p = e % AD_P;
+                    const int j = j0 + p;
+                    const bool ok = s < d.ns && j < nin;
+                    cp_async1<T>(sb + (uint32_t)((s * RS + p) * sizeof(T)),
+                                 ok ? Xo + __ldg(tx + j) + d.xoff[s] : Xo, ok);
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    const int pg = tid >> 3, tg = tid & 7;   // positions 4 pg + i, new combinations 4 tg + j
+    T mx = 0;
+    issue(0, 0);
+    issue(1, 1);
+    int b = 0;
+    for (int64_t k = 0; k < mine; ++k) {
+        cp_async_wait<1>();
+        // tile k landed everywhere; every thread is done with tile k - 1
+        __syncthreads();
+        issue(k + 2, b == 0 ? 2 : b - 1);
+        const T *xb = Xs + b * TB;
+        T acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+        if (XM == 2) {
+            for (int s = 0; s < ns4; s += 4) {
+                T xv[4][4], wv[4][4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) ld4(xb + (4 * pg + i) * RS + s, xv[i]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) ld4(Ws + (s + q) * WR + 4 * tg, wv[q]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[i][j] += xv[i][q] * wv[q][j];
+            }
+        } else {
+            for (int s = 0; s < ns4; ++s) {
+                T xv[4], wv[4];
+                ld4(xb + s * RS + 4 * pg, xv);
+                ld4(Ws + s * WR + 4 * tg, wv);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] += xv[i] * wv[j];
+            }
+        }
+        // results straight from registers, along Y's contiguous direction
+        {
+            int64_t crem;
+            const int64_t o = div_tile((int64_t)blockIdx.x + k * gridDim.x, nch, lnch, crem);
+            int64_t bx = 0, by = 0;
+            absorb_outer(d, o, nod, bx, by);
+            T *Yo = Y + by;
+            const int j0 = (int)crem * AD_P + 4 * pg;
+            const int t0 = 4 * tg;
+            if (ym == 1) {
+                if (j0 < nin) {
+                    const int oy = __ldg(ty + j0);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (t0 + j >= d.nt) break;
+                        st4(Yo + oy + d.yoff[t0 + j], acc[0][j] * scale, acc[1][j] * scale,
+                            acc[2][j] * scale, acc[3][j] * scale);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) mx = mx > acc[i][j] ? mx : acc[i][j];
+                    }
+                }
+            } else if (ym == 2) {
+                if (t0 < d.nt) {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        if (j0 + i >= nin) break;
+                        st4(Yo + __ldg(ty + j0 + i) + d.yoff[t0], acc[i][0] * scale,
+                            acc[i][1] * scale, acc[i][2] * scale, acc[i][3] * scale);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) mx = mx > acc[i][j] ? mx : acc[i][j];
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (j0 + i >= nin) break;
+                    const int oy = __ldg(ty + j0 + i);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if (t0 + j >= d.nt) break;
+                        Yo[oy + d.yoff[t0 + j]] = acc[i][j] * scale;
+                        mx = mx > acc[i][j] ? mx : acc[i][j];
+                    }
+                }
+            }
+        }
+        b = b == 2 ? 0 : b + 1;
+    }
+    cp_async_wait<0>();
+    if (d.mxy) block_max_atomic(d.mxy + beta, (double)mx * (double)scale);
+}
+
+constexpr int RD_P = 64;    // positions per tile
+constexpr int RD_S = 3;     // tile buffers
+
+template <typename T>
+__host__ __device__ constexpr size_t reduce_dense_smem() {
+    // tiles [RD_S][64 rows: X s, then Z t][RD_P + pad]; the final per-group
+    // sums [4][1024] reuse them
+    return (size_t)RD_S * 64 * (RD_P + ad_pad<T>()) * sizeof(T);
+}
+
+// vm bit 0: four consecutive positions of X per copy, bit 1: the same for Z.
+template <typename T>
+__global__ void __launch_bounds__(256) k_reduce_dense(const __grid_constant__ RDesc d, int vm,
+                                                      int64_t chunk, int nchunks, T *part) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    constexpr int RR = RD_P + ad_pad<T>();
+    constexpr int TB = 64 * RR;
+    T *Ts = (T *)smraw;
+    const int tid = threadIdx.x;
+    const int nin = (int)d.nin;
+    const int *tx = d.tab, *tz = d.tab + nin;
+    const int nod = d.nmd - d.nin_d;
+    const int64_t g = (int64_t)blockIdx.y + (int64_t)gridDim.y * blockIdx.z;
+    if (g >= d.ng * d.nbeta) return;
+    const int64_t beta = g / d.ng, gi = g - beta * d.ng;
+    int64_t gx = beta * d.bsx, gz = beta * d.bsz, go = 0;
+    group_offsets(d, gi, gx, gz, go);
+    const T sx = d.mxx ? pow2neg<T>(exp_of_bits(d.mxx[beta * d.mxx_bs])) : T(1);
+    const T sz = d.mxz ? pow2neg<T>(exp_of_bits(d.mxz[beta * d.mxz_bs])) : T(1);
+    const int64_t cper = (nin + RD_P - 1) / RD_P;
+    const int64_t ntile = d.nouter * cper;
+    const int64_t t0 = (int64_t)blockIdx.x * chunk;
+    const int64_t t1 = t0 + chunk < ntile ? t0 + chunk : ntile;
+    const int nk = t1 > t0 ? (int)(t1 - t0) : 0;
+    const int lcper = log2_if_pow2(cper);
+    const T *X = (const T *)d.X, *Z = (const T *)d.Z;
+    const uint32_t ts0 = (uint32_t)__cvta_generic_to_shared(Ts);
+    auto issue = [&](int k, int b) {
+        if (k < nk) {
+            int64_t crem;
+            const int64_t o = div_tile(t0 + k, cper, lcper, crem);
+            int64_t cbx = gx, cbz = gz;
+            reduce_outer(d, o, nod, cbx, cbz);
+            const int j0 = (int)crem * RD_P;
+            const uint32_t sb = ts0 + (uint32_t)(b * TB * sizeof(T));
+            // X rows 0..31, Z rows 32..63
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const T *base = h ? Z + cbz : X + cbx;
+                const int *tab = h ? tz : tx;
+                const int nv = h ? d.nt : d.ns;
+                const bool v4 = (vm >> h) & 1;
+                if (v4) {
+                    for (int e = tid; e < 32 * (RD_P / 4); e += 256) {
+                        const int v = e / (RD_P / 4), p = (e % (RD_P / 4)) * 4;
+                        const int j = j0 + p;
+                        const bool ok = v < nv && j < nin;
+                        const int64_t off = h ? d.zoff[v < 32 ? v : 0] : d.xoff[v < 32 ? v : 0];
+                        cp_async4<T>(sb + (uint32_t)(((32 * h + v) * RR + p) * sizeof(T)),
+                                     ok ? base + __ldg(tab + j) + off : base, ok);
+                    }
+                } else {
+                    for (int e = tid; e < 32 * RD_P; e += 256) {
+                        const int v = e / RD_P, p = e % RD_P;
+                        const int j = j0 + p;
+                        const bool ok = v < nv && j < nin;
+                        const int64_t off = h ? d.zoff[v] : d.xoff[v];
+                        cp_async1<T>(sb + (uint32_t)(((32 * h + v) * RR + p) * sizeof(T)),
+                                     ok ? base + __ldg(tab + j) + off : base, ok);
+                    }
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    // thread: positions [16 pq, 16 pq + 16) of each tile, outputs
+    // s = ts + 8 i, t = tt + 8 j (i, j < 4)
+    const int pq = tid >> 6, ts = (tid >> 3) & 7, tt = tid & 7;
+    T acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+    issue(0, 0);
+    issue(1, 1);
+    int b = 0;
+    for (int k = 0; k < nk; ++k) {
+        cp_async_wait<1>();
+        __syncthreads();
+        issue(k + 2, b == 0 ? 2 : b - 1);
+        const T *tb = Ts + b * TB;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int p = 16 * pq + 4 * q;
+            T xv[4][4], zv[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) ld4(tb + (ts + 8 * i) * RR + p, xv[i]);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) ld4(tb + (32 + tt + 8 * j) * RR + p, zv[j]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] += xv[i][u] * zv[j][u];
+        }
+        b = b == 2 ? 0 : b + 1;
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+    // the four position groups' sums, then this block's partial row
+    T *red = Ts;   // [4][1024]
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) red[pq * 1024 + (ts + 8 * i) * 32 + tt + 8 * j] = acc[i][j];
+    __syncthreads();
+    const T scale = sx * sz;
+    T *prow = part + (g * nchunks + blockIdx.x) * 1024;
+    for (int o = tid; o < 1024; o += 256)
+        prow[o] = ((red[o] + red[1024 + o]) + (red[2048 + o] + red[3072 + o])) * scale;
+    __threadfence();
+    __syncthreads();
+    __shared__ bool last;
+    if (tid == 0) last = atomicAdd(d.cnt + g, 1u) == (unsigned)(nchunks - 1);
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const T *pg = part + g * nchunks * 1024;
+    T mx = 0;
+    for (int o = tid; o < 1024; o += 256) {
+        const int s = o >> 5, t = o & 31;
+        T v = 0;
+        for (int c = 0; c < nchunks; ++c) v += __ldcg(pg + (int64_t)c * 1024 + o);
+        if (s < d.ns && t < d.nt) {
+            ((T *)d.O)[go + beta * d.bso + d.oso[s] + d.oto[t]] = v;
+            mx = mx > v ? mx : v;
+        }
+    }
+    if (d.mxo) block_max_atomic(d.mxo + beta, (double)mx);
+    if (tid == 0) d.cnt[g] = 0u;
+}
+
+}  // namespace tn

@@ -662,7 +662,7 @@ static bool make_absorb(const std::vector<int> &card, const Labels &lx, bool bx,
                         int64_t perw, const void *W, const unsigned long long *mxw,
                         const Labels &ly, bool by, int64_t pery, void *Y,
                         unsigned long long *mxy, const Labels *sorder, int nbeta,
-                        int32_t *argmax, ADesc &d) {
+                        int32_t *argmax, ADesc &d, bool dense_ok = false) {
     std::memset(&d, 0, sizeof d);
     if (by != (bx || bw)) { absorb_reject = "batch label"; return false; }
     std::set<int> sx(lx.begin(), lx.end()), sw(lw.begin(), lw.end()), sy(ly.begin(), ly.end());
@@ -677,11 +677,15 @@ static bool make_absorb(const std::vector<int> &card, const Labels &lx, bool bx,
     }
     if (!combo_offsets(card, S, lx, sx, lw, sw, AMAX, d.ns, d.xoff, d.wso)) { absorb_reject = "summed combinations"; return false; }
     if (!combo_offsets(card, T, ly, sy, lw, sw, AMAX, d.nt, d.yoff, d.wto)) { absorb_reject = "new combinations"; return false; }
+    // more than 256 combinations: the dense kernel (sum-product, W holding
+    // no position label; checked below)
+    bool dense = false;
     {
         int ps = 1, pt = 1;
         while (ps < d.ns) ps <<= 1;
         while (pt < d.nt) pt <<= 1;
-        if (ps * pt > 256) { absorb_reject = "combination product"; return false; }
+        dense = ps * pt > 256;
+        if (dense && !dense_ok) { absorb_reject = "combination product"; return false; }
     }
     std::vector<SDim> raw;
     for (int v : R)
@@ -754,6 +758,7 @@ static bool make_absorb(const std::vector<int> &card, const Labels &lx, bool bx,
         }
         d.nsh = (int)c;
     }
+    if (dense && d.nsh != 1) { absorb_reject = "combination product"; return false; }
     d.nbeta = by ? nbeta : 1;
     d.bsx = (by && bx) ? perx : 0;
     d.bsw = (by && bw) ? perw : 0;
@@ -1520,13 +1525,13 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                             mxp(P.fwd[nd.a].mx), nb.labels, nb.beta, P.fwd[nd.b].per, fptr(nd.b),
                             mxp(P.fwd[nd.b].mx), nd.labels, nd.beta, P.fwd[id].per, outp,
                             mxp(P.fwd[id].mx), &nd.elim, nbeta,
-                            maxplus ? P.am + P.am_off[id] : nullptr, st.ad) ||
+                            maxplus ? P.am + P.am_off[id] : nullptr, st.ad, !maxplus) ||
                 ((st.why = absorb_reject), false) ||
                 make_absorb(net.card, nb.labels, nb.beta, P.fwd[nd.b].per, fptr(nd.b),
                             mxp(P.fwd[nd.b].mx), na.labels, na.beta, P.fwd[nd.a].per, fptr(nd.a),
                             mxp(P.fwd[nd.a].mx), nd.labels, nd.beta, P.fwd[id].per, outp,
                             mxp(P.fwd[id].mx), &nd.elim, nbeta,
-                            maxplus ? P.am + P.am_off[id] : nullptr, st.ad)) {
+                            maxplus ? P.am + P.am_off[id] : nullptr, st.ad, !maxplus)) {
                 st.kind = 2;
             } else if (!maxplus &&
                        make_reduce(net.card, na.labels, na.beta, P.fwd[nd.a].per, fptr(nd.a),
@@ -1610,12 +1615,12 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                                 P.mx + P.adj[id].mx, nb.labels, nb.beta, P.fwd[nd.b].per,
                                 bfptr(nd.b), P.mx + P.fwd[nd.b].mx, na.labels, P.adj_beta[nd.a],
                                 P.adj[nd.a].per, aptr(nd.a), P.mx + P.adj[nd.a].mx, nullptr, nbeta,
-                                nullptr, st.ad) ||
+                                nullptr, st.ad, true) ||
                     make_absorb(net.card, nb.labels, nb.beta, P.fwd[nd.b].per, bfptr(nd.b),
                                 P.mx + P.fwd[nd.b].mx, nd.labels, P.adj_beta[id], P.adj[id].per,
                                 cbar, P.mx + P.adj[id].mx, na.labels, P.adj_beta[nd.a],
                                 P.adj[nd.a].per, aptr(nd.a), P.mx + P.adj[nd.a].mx, nullptr, nbeta,
-                                nullptr, st.ad)) {
+                                nullptr, st.ad, true)) {
                     st.kind = 2;
                 } else if (make_bgemm(net.card, nd.labels, P.adj_beta[id], P.adj[id].per, cbar,
                                       P.mx + P.adj[id].mx, nb.labels, nb.beta, P.fwd[nd.b].per,
@@ -1649,12 +1654,12 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                                  P.mx + P.fwd[nd.a].mx, nd.labels, P.adj_beta[id], P.adj[id].per,
                                  cbar, P.mx + P.adj[id].mx, nb.labels, P.adj_beta[nd.b],
                                  P.adj[nd.b].per, aptr(nd.b), P.mx + P.adj[nd.b].mx, nullptr,
-                                 nbeta, nullptr, st.ad) ||
+                                 nbeta, nullptr, st.ad, true) ||
                      make_absorb(net.card, nd.labels, P.adj_beta[id], P.adj[id].per, cbar,
                                  P.mx + P.adj[id].mx, na.labels, na.beta, P.fwd[nd.a].per,
                                  bfptr(nd.a), P.mx + P.fwd[nd.a].mx, nb.labels, P.adj_beta[nd.b],
                                  P.adj[nd.b].per, aptr(nd.b), P.mx + P.adj[nd.b].mx, nullptr,
-                                 nbeta, nullptr, st.ad))) {
+                                 nbeta, nullptr, st.ad, true))) {
                     st.kind = 2;
                 } else if (make_reduce(net.card, na.labels, na.beta, P.fwd[nd.a].per, bfptr(nd.a),
                                 P.mx + P.fwd[nd.a].mx, nd.labels, P.adj_beta[id], P.adj[id].per,

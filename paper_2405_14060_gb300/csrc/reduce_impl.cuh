@@ -17,21 +17,11 @@
 #include <mutex>
 #include <vector>
 
+#include "dense_impl.cuh"
 #include "devutil.cuh"
 #include "stream.cuh"
 
 namespace tn {
-
-__device__ __forceinline__ void group_offsets(const RDesc &d, int64_t gi, int64_t &ox,
-                                              int64_t &oz, int64_t &oo) {
-    for (int i = d.ngd - 1; i >= 0; --i) {
-        int64_t dg = gi % d.gsz[i];
-        gi /= d.gsz[i];
-        ox += dg * d.gsx[i];
-        oz += dg * d.gsz2[i];
-        oo += dg * d.gso[i];
-    }
-}
 
 // 16-byte vectors of T and the few operations the reduce kernels need on them.
 template <typename T> struct Vec16;
@@ -154,27 +144,6 @@ __device__ __forceinline__ void reduce_finish(const RDesc &d, T (&acc)[NS][NT], 
     }
     if (d.mxo) block_max_atomic(d.mxo + beta, (double)mx);
     if (threadIdx.x == 0) d.cnt[g] = 0u;
-}
-
-// Outer decode of the summed positions: operand offsets of outer index o.
-__device__ __forceinline__ void reduce_outer(const RDesc &d, int64_t o, int nod, int64_t &cbx,
-                                             int64_t &cbz) {
-    if (d.pow2m) {
-        const int64_t r0 = o * d.nin;
-        for (int q = 0; q < nod; ++q) {
-            int64_t dg = (r0 >> d.msh[q]) & (int64_t)(d.msz[q] - 1);
-            cbx += dg * d.msx[q];
-            cbz += dg * d.msz2[q];
-        }
-    } else {
-        int64_t r = o;
-        for (int q = nod - 1; q >= 0; --q) {
-            int64_t dg = r % d.msz[q];
-            r /= d.msz[q];
-            cbx += dg * d.msx[q];
-            cbz += dg * d.msz2[q];
-        }
-    }
 }
 
 // The summed positions m split into inner ones (offset table computed at plan
@@ -445,8 +414,64 @@ static std::vector<RedPiece> reduce_pieces(const RDesc &d, int esz) {
     return out;
 }
 
+// Dense form (k_reduce_dense): more than 256 outputs per group after
+// rounding to powers of two.  Its chunking: about three resident blocks per
+// SM over all groups.
+static bool reduce_dense_form(const RDesc &d) {
+    return pow2ceil_i(d.ns) * pow2ceil_i(d.nt) > 256;
+}
+static void reduce_dense_shape(const RDesc &d, int64_t &chunk, int &nchunks) {
+    const int64_t groups = std::max<int64_t>(1, d.ng * d.nbeta);
+    const int64_t ntile = d.nouter * ((d.nin + RD_P - 1) / RD_P);
+    const int64_t want = std::max<int64_t>(1, (152LL * 3) / groups);
+    chunk = std::max<int64_t>(1, (ntile + want - 1) / want);
+    nchunks = (int)std::max<int64_t>(1, (ntile + chunk - 1) / chunk);
+}
+// 16-byte copies of four consecutive positions (bit 0: X, bit 1: Z) where
+// every aligned quad of positions is contiguous and 16-byte aligned.
+static int reduce_dense_vm(const RDesc &d) {
+    const int L = d.nmd - 1;   // the fastest summed dim
+    auto ok = [&](const void *p, int64_t bs, const int64_t *ms, const int64_t *gs,
+                  const int64_t *off, int n) {
+        if (((uintptr_t)p & 15) || bs % 4 || d.nin % 4 || d.msz[L] % 4 || ms[L] != 1) return false;
+        for (int k = 0; k < L; ++k)
+            if (ms[k] % 4) return false;
+        for (int k = 0; k < d.ngd; ++k)
+            if (gs[k] % 4) return false;
+        for (int i = 0; i < n; ++i)
+            if (off[i] % 4) return false;
+        return true;
+    };
+    return (ok(d.X, d.bsx, d.msx, d.gsx, d.xoff, d.ns) ? 1 : 0) |
+           (ok(d.Z, d.bsz, d.msz2, d.gsz2, d.zoff, d.nt) ? 2 : 0);
+}
+
+template <typename T>
+static void reduce_dense_go(const RDesc &d, void *scratch, cudaStream_t st) {
+    const int64_t groups = d.ng * d.nbeta;
+    int64_t chunk;
+    int nchunks;
+    reduce_dense_shape(d, chunk, nchunks);
+    constexpr size_t smem = reduce_dense_smem<T>();
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(k_reduce_dense<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    });
+    dim3 grid((unsigned)nchunks, (unsigned)std::min<int64_t>(groups, 65535),
+              (unsigned)((groups + 65534) / 65535));
+    k_reduce_dense<T><<<grid, 256, smem, st>>>(d, reduce_dense_vm(d), chunk, nchunks,
+                                               (T *)scratch);
+}
+
 #ifdef TN_STREAM_HOST_DEFS
 size_t reduce_scratch_bytes(const RDesc &d, int elem_bytes) {
+    if (reduce_dense_form(d)) {
+        int64_t chunk;
+        int nchunks;
+        reduce_dense_shape(d, chunk, nchunks);
+        return (size_t)(d.ng * d.nbeta * nchunks) * 1024 * (size_t)elem_bytes;
+    }
     size_t mx = 0;
     for (auto &p : reduce_pieces(d, elem_bytes)) {
         const int nch = std::max(p.nchunks, p.vec ? p.vnchunks : 0);
@@ -495,6 +520,10 @@ static void reduce_nt(const RDesc &d, const RedPiece &p, void *scratch, cudaStre
 template <typename T>
 void launch_reduce(const RDesc &d, void *scratch, cudaStream_t st) {
     if (d.ng * d.nbeta == 0) return;
+    if (reduce_dense_form(d)) {
+        reduce_dense_go<T>(d, scratch, st);
+        return;
+    }
     for (const RedPiece &p : reduce_pieces(d, (int)sizeof(T))) {
         RDesc c = d;
         c.ns = p.ns;
@@ -510,8 +539,11 @@ void launch_reduce(const RDesc &d, void *scratch, cudaStream_t st) {
 }
 
 #ifdef TN_STREAM_HOST_DEFS
-int reduce_launches(const RDesc &d) { return (int)reduce_pieces(d, 4).size(); }
+int reduce_launches(const RDesc &d) {
+    return reduce_dense_form(d) ? 1 : (int)reduce_pieces(d, 4).size();
+}
 bool reduce_vector_form(const RDesc &d, int elem_bytes) {
+    if (reduce_dense_form(d)) return reduce_dense_vm(d) == 3;
     const auto pieces = reduce_pieces(d, elem_bytes);
     return !pieces.empty() && pieces[0].vec && ((uintptr_t)d.X % 16) == 0 &&
            ((uintptr_t)d.Z % 16) == 0;

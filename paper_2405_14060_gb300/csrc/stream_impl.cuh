@@ -20,6 +20,7 @@
 #include <mutex>
 #include <vector>
 
+#include "dense_impl.cuh"
 #include "devutil.cuh"
 #include "stream.cuh"
 
@@ -351,10 +352,73 @@ static int pow2ceil(int v) {
     return p;
 }
 
+// Launch modes of the dense absorb (host): 16-byte copies and stores where
+// every aligned quad of consecutive entries is contiguous and 16-byte aligned.
+static DenseModes absorb_dense_modes(const ADesc &d) {
+    DenseModes m{0, 0};
+    const int L = d.nrd - 1;   // the fastest position dim
+    auto aligned = [](const void *p) { return ((uintptr_t)p & 15) == 0; };
+    auto strides4 = [&](const int64_t *st, int skip) {
+        for (int k = 0; k < d.nrd; ++k)
+            if (k != skip && st[k] % 4) return false;
+        return true;
+    };
+    auto offs4 = [](const int32_t *o, int n) {
+        for (int i = 0; i < n; ++i)
+            if (o[i] % 4) return false;
+        return true;
+    };
+    auto quads = [](const int32_t *o, int n) {
+        if (n % 4) return false;
+        for (int i = 0; i < n; ++i)
+            if (o[i] != o[i & ~3] + (i & 3)) return false;
+        return true;
+    };
+    const bool pos4 = d.nin % 4 == 0 && d.rsz[L] % 4 == 0;
+    if (aligned(d.X) && d.bsx % 4 == 0) {
+        if (pos4 && d.rsx[L] == 1 && strides4(d.rsx, L) && offs4(d.xoff, d.ns)) m.xm = 1;
+        else if (strides4(d.rsx, -1) && quads(d.xoff, d.ns) && offs4(d.xoff, d.ns)) m.xm = 2;
+    }
+    if (aligned(d.Y) && d.bsy % 4 == 0) {
+        if (pos4 && d.rsy[L] == 1 && strides4(d.rsy, L) && offs4(d.yoff, d.nt)) m.ym = 1;
+        else if (strides4(d.rsy, -1) && quads(d.yoff, d.nt) && offs4(d.yoff, d.nt)) m.ym = 2;
+    }
+    return m;
+}
+
+template <typename T, int XM>
+static void absorb_dense_go(const ADesc &d, int ym, cudaStream_t st) {
+    constexpr size_t smem = absorb_dense_smem<T>();
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute(k_absorb_dense<T, XM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    });
+    const int bps = (int)std::max<size_t>(1, (227 * 1024) / (smem + 1024));
+    const int64_t ntile = d.nouter * ((d.nin + AD_P - 1) / AD_P);
+    const int64_t cap = std::max<int64_t>(1, (152LL * bps) / std::max(1, d.nbeta));
+    dim3 grid((unsigned)std::max<int64_t>(1, std::min(ntile, cap)), (unsigned)d.nbeta, 1);
+    k_absorb_dense<T, XM><<<grid, 256, smem, st>>>(d, ym);
+}
+
+// Does the absorb run as k_absorb_dense (more than 256 combinations after
+// rounding to powers of two; sum-product with W holding no position label)?
+static bool absorb_dense_form(const ADesc &d) {
+    return pow2ceil(d.ns) * pow2ceil(d.nt) > 256;
+}
+
 template <typename T>
 void launch_absorb(const ADesc &d0, int semiring, cudaStream_t st) {
     if (d0.nr * d0.nbeta == 0) return;
     ADesc d = d0;
+    if (absorb_dense_form(d)) {
+        if (semiring != SUM || d.nsh != 1 || d.ns > 32 || d.nt > 32) return;
+        const DenseModes m = absorb_dense_modes(d);
+        if (m.xm == 1) absorb_dense_go<T, 1>(d, m.ym, st);
+        else if (m.xm == 2) absorb_dense_go<T, 2>(d, m.ym, st);
+        else absorb_dense_go<T, 0>(d, m.ym, st);
+        return;
+    }
     // the kernel runs on the next powers of two; the extra combinations are
     // skipped by warp-uniform guards
     int ns = pow2ceil(d.ns), nt = pow2ceil(d.nt);

@@ -52,6 +52,58 @@ def test_pr_mar_small_fp64(name, mk, method):
     _marg_close(M, marg[0], marg_ref, 1e-10)
 
 
+def _dense_model(layout, seed):
+    """Three factors A(r, s), W(s, t), V(t, r): r = 12 binary variables (4096
+    positions), s = cards (3, 2, 2, 2) (24 summed combinations), t = cards
+    (5, 2, 2) (20 new ones).  With the tree ((A, W'), V'), where W' collects
+    the unity vectors of s and t and V' those of r, the node (A, W') is a
+    dense absorb (24 x 20 combinations, more than the register-blocked
+    kernels take), its adjoint A-bar another (20 x 24) and W'-bar a dense
+    reduce.  layout "sfast": A's summed labels fastest (four at a time);
+    "mixed": A's labels interleaved (one entry at a time)."""
+    rng = np.random.default_rng(seed)
+    r, s, t = list(range(12)), [12, 13, 14, 15], [16, 17, 18]
+    card = np.array([2] * 12 + [3, 2, 2, 2] + [5, 2, 2], np.int32)
+    sa = r + s if layout == "sfast" else [s[0]] + r[:6] + [s[1], s[2]] + r[6:] + [s[3]]
+    scopes = [np.array(sa, np.int32), np.array(s + t, np.int32), np.array(t + r, np.int32)]
+    tables = [rng.uniform(0.5, 1.5, size=int(np.prod(card[sc]))) for sc in scopes]
+    m = synth.Model(card, scopes, tables, "MARKOV", "dense_" + layout)
+    nleaves = 3 + m.nvars
+    left, right, nid = [], [], nleaves
+    w = 1
+    for v in s + t:
+        left.append(w), right.append(3 + v)
+        w, nid = nid, nid + 1
+    vv = 2
+    for v in r:
+        left.append(vv), right.append(3 + v)
+        vv, nid = nid, nid + 1
+    left.append(0), right.append(w)
+    c, nid = nid, nid + 1
+    left.append(c), right.append(vv)
+    return m, left, right
+
+
+@pytest.mark.parametrize("layout", ["sfast", "mixed"])
+def test_dense_absorb_and_reduce_nodes(layout):
+    m, left, right = _dense_model(layout, 7)
+    M = tn.Model.from_synth(m)
+    M.set_order(left, right)
+    rng = np.random.default_rng(3)
+    ev = np.stack([np.full(m.nvars, -1, np.int32)] +
+                  [synth.random_evidence(m, 0.15, rng) for _ in range(2)])
+    refs = [oracle.ve_mar(m, e) for e in ev]
+    lz, marg = M.mar(ev, prec="fp64")
+    for b, (lz_ref, marg_ref) in enumerate(refs):
+        assert abs(lz[b] - lz_ref) < 1e-10
+        _marg_close(M, marg[b], marg_ref, 1e-10)
+    for prec in ("fp32", "bf16"):
+        lz, marg = M.mar(ev, prec=prec)
+        for b, (lz_ref, marg_ref) in enumerate(refs):
+            assert abs(lz[b] - lz_ref) <= 1e-4 * abs(lz_ref)
+            _marg_close(M, marg[b], marg_ref, 1e-3)
+
+
 @pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16"])
 def test_pr_mar_small_reduced(prec):
     m = synth.grid_ising(4, 5)
