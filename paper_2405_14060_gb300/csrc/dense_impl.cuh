@@ -102,9 +102,10 @@ __device__ __forceinline__ void cp_async1(uint32_t s, const T *g, bool ok) {
 
 // Launch modes of the dense absorb, chosen on the host from the descriptor:
 // X: 0 one entry per copy into [s][p], 1 four positions per copy into
-// [s][p], 2 four summed combinations per copy into [p][s];
+// [s][p], 2 four summed combinations per copy into [p][s], 3 the tile's
+// 16-byte chunks in memory order (planned table), scattered into [s][p];
 // Y: 0 one entry per store, 1 four positions per store, 2 four new
-// combinations per store.
+// combinations per store, 3 the tile's chunks through shared memory.
 struct DenseModes {
     int xm, ym;
 };
@@ -116,11 +117,18 @@ template <typename T>
 __host__ __device__ constexpr int ad_pad() {
     return 16 / (int)sizeof(T);
 }
-template <typename T>
+// Entries of one tile buffer for X mode XM: [s][p] (0, 1), [p][s] (2), the
+// tile's chunks in memory order (3).
+template <typename T, int XM>
+__host__ __device__ constexpr int ad_buf() {
+    return XM == 3 ? 32 * AD_P : XM == 2 ? AD_P * (32 + ad_pad<T>()) : 32 * (AD_P + ad_pad<T>());
+}
+template <typename T, int XM>
 __host__ __device__ constexpr size_t absorb_dense_smem() {
-    // W [32][32 + pad], tiles [AD_S][32 x (AD_P + pad)] (either layout fits)
-    return ((size_t)32 * (32 + ad_pad<T>()) +
-            (size_t)AD_S * std::max(32 * (AD_P + ad_pad<T>()), AD_P * (32 + ad_pad<T>()))) *
+    // W [32][32 + pad], tile buffers, and in chunk mode the [s][p] tile the
+    // chunks are scattered into
+    return ((size_t)32 * (32 + ad_pad<T>()) + (size_t)AD_S * ad_buf<T, XM>() +
+            (XM == 3 ? (size_t)32 * (AD_P + ad_pad<T>()) : 0)) *
            sizeof(T);
 }
 
@@ -145,21 +153,37 @@ __device__ __forceinline__ void absorb_outer(const ADesc &d, int64_t o, int nod,
     }
 }
 
+// Four entries of a tile buffer scattered to (or gathered from) the 16-bit
+// shared-memory slots packed in w.
+template <typename T>
+__device__ __forceinline__ void scatter4(T *dst, uint2 w, const T (&v)[4]) {
+    dst[w.x & 0xffffu] = v[0];
+    dst[w.x >> 16] = v[1];
+    dst[w.y & 0xffffu] = v[2];
+    dst[w.y >> 16] = v[3];
+}
+
+// ym: 0 one entry per store, 1 four positions per store, 2 four new
+// combinations per store (all from registers), 3 through shared memory as
+// the tile's chunks in memory order (chunk table at d.cyo).
 template <typename T, int XM>
 __global__ void __launch_bounds__(256) k_absorb_dense(const __grid_constant__ ADesc d, int ym) {
     extern __shared__ __align__(16) unsigned char smraw[];
     constexpr int PAD = ad_pad<T>();
-    constexpr int WR = 32 + PAD;                                  // W row: [s][t]
-    constexpr int RS = XM == 2 ? 32 + PAD : AD_P + PAD;           // tile row
-    constexpr int TB = XM == 2 ? AD_P * RS : 32 * RS;             // tile buffer
+    constexpr int WR = 32 + PAD;                       // W row: [s][t]
+    constexpr int RS = AD_P + PAD;                     // [s][p] / [t][p] row
+    constexpr int RX = XM == 2 ? 32 + PAD : RS;        // row of the tile buffers
+    constexpr int TB = ad_buf<T, XM>();
     T *Ws = (T *)smraw;
     T *Xs = Ws + 32 * WR;
+    T *Xc = Xs + AD_S * TB;                            // chunk mode: [s][p]
     const int tid = threadIdx.x;
     const int nin = (int)d.nin;
     const int *tx = d.tab, *ty = d.tab + nin;
     const int nod = d.nrd - d.nin_d;
     const int64_t beta = blockIdx.y;
     const int ns4 = (d.ns + 3) & ~3;
+    const int nqx = d.ns * (AD_P / 4), nqy = d.nt * (AD_P / 4);
     {
         const T *Wg = (const T *)d.W + beta * d.bsw;
         for (int i = tid; i < 32 * 32; i += 256) {
@@ -188,22 +212,27 @@ __global__ void __launch_bounds__(256) k_absorb_dense(const __grid_constant__ AD
             const int j0 = (int)crem * AD_P;
             const T *Xo = X + bx;
             const uint32_t sb = xs0 + (uint32_t)(b * TB * sizeof(T));
-            if (XM == 1) {
+            if (XM == 3) {
+                const T *Xt = Xo + __ldg(tx + j0);
+                const int32_t *crel = d.tab + d.cxo;
+                for (int q = tid; q < nqx; q += 256)
+                    cp_async4<T>(sb + (uint32_t)(4 * q * sizeof(T)), Xt + __ldg(crel + q), true);
+            } else if (XM == 1) {
                 // 32 rows x 32 quads of positions
                 for (int e = tid; e < 32 * (AD_P / 4); e += 256) {
                     const int s = e / (AD_P / 4), p = (e % (AD_P / 4)) * 4;
                     const int j = j0 + p;
                     const bool ok = s < d.ns && j < nin;
-                    cp_async4<T>(sb + (uint32_t)((s * RS + p) * sizeof(T)),
+                    cp_async4<T>(sb + (uint32_t)((s * RX + p) * sizeof(T)),
                                  ok ? Xo + __ldg(tx + j) + d.xoff[s] : Xo, ok);
                 }
             } else if (XM == 2) {
-                // AD_P rows x (ns / 4) quads of summed combinations
+                // AD_P rows x 8 quads of summed combinations
                 for (int e = tid; e < AD_P * 8; e += 256) {
                     const int p = e >> 3, s = (e & 7) * 4;
                     const int j = j0 + p;
                     const bool ok = s < d.ns && j < nin;
-                    cp_async4<T>(sb + (uint32_t)((p * RS + s) * sizeof(T)),
+                    cp_async4<T>(sb + (uint32_t)((p * RX + s) * sizeof(T)),
                                  ok ? Xo + __ldg(tx + j) + d.xoff[s] : Xo, ok);
                 }
             } else {
@@ -211,7 +240,7 @@ __global__ void __launch_bounds__(256) k_absorb_dense(const __grid_constant__ AD
                     const int s = e / AD_P, p = e % AD_P;
                     const int j = j0 + p;
                     const bool ok = s < d.ns && j < nin;
-                    cp_async1<T>(sb + (uint32_t)((s * RS + p) * sizeof(T)),
+                    cp_async1<T>(sb + (uint32_t)((s * RX + p) * sizeof(T)),
                                  ok ? Xo + __ldg(tx + j) + d.xoff[s] : Xo, ok);
                 }
             }
@@ -228,7 +257,18 @@ __global__ void __launch_bounds__(256) k_absorb_dense(const __grid_constant__ AD
         // tile k landed everywhere; every thread is done with tile k - 1
         __syncthreads();
         issue(k + 2, b == 0 ? 2 : b - 1);
-        const T *xb = Xs + b * TB;
+        T *tb = Xs + b * TB;
+        const T *xb = tb;
+        if (XM == 3) {
+            const uint2 *cs = (const uint2 *)(d.tab + d.cxo + nqx);
+            for (int q = tid; q < nqx; q += 256) {
+                T v[4];
+                ld4(tb + 4 * q, v);
+                scatter4(Xc, __ldg(cs + q), v);
+            }
+            __syncthreads();
+            xb = Xc;
+        }
         T acc[4][4];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -238,7 +278,7 @@ __global__ void __launch_bounds__(256) k_absorb_dense(const __grid_constant__ AD
             for (int s = 0; s < ns4; s += 4) {
                 T xv[4][4], wv[4][4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) ld4(xb + (4 * pg + i) * RS + s, xv[i]);
+                for (int i = 0; i < 4; ++i) ld4(xb + (4 * pg + i) * RX + s, xv[i]);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) ld4(Ws + (s + q) * WR + 4 * tg, wv[q]);
 #pragma unroll
@@ -249,7 +289,9 @@ __global__ void __launch_bounds__(256) k_absorb_dense(const __grid_constant__ AD
                         for (int j = 0; j < 4; ++j) acc[i][j] += xv[i][q] * wv[q][j];
             }
         } else {
-            for (int s = 0; s < ns4; ++s) {
+            // chunk mode fills only the rows s < ns
+            const int send = XM == 3 ? d.ns : ns4;
+            for (int s = 0; s < send; ++s) {
                 T xv[4], wv[4];
                 ld4(xb + s * RS + 4 * pg, xv);
                 ld4(Ws + s * WR + 4 * tg, wv);
@@ -259,49 +301,67 @@ __global__ void __launch_bounds__(256) k_absorb_dense(const __grid_constant__ AD
                     for (int j = 0; j < 4; ++j) acc[i][j] += xv[i] * wv[j];
             }
         }
-        // results straight from registers, along Y's contiguous direction
-        {
-            int64_t crem;
-            const int64_t o = div_tile((int64_t)blockIdx.x + k * gridDim.x, nch, lnch, crem);
-            int64_t bx = 0, by = 0;
-            absorb_outer(d, o, nod, bx, by);
-            T *Yo = Y + by;
-            const int j0 = (int)crem * AD_P + 4 * pg;
-            const int t0 = 4 * tg;
-            if (ym == 1) {
-                if (j0 < nin) {
-                    const int oy = __ldg(ty + j0);
+        int64_t crem;
+        const int64_t o = div_tile((int64_t)blockIdx.x + k * gridDim.x, nch, lnch, crem);
+        int64_t bx = 0, by = 0;
+        absorb_outer(d, o, nod, bx, by);
+        T *Yo = Y + by;
+        const int j0 = (int)crem * AD_P + 4 * pg;
+        const int t0 = 4 * tg;
+        if (ym == 3) {
+            // [t][p] in shared memory, then the tile's chunks in memory order
+            T *ys = XM == 3 ? Xc : tb;
+            __syncthreads();
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        if (t0 + j >= d.nt) break;
-                        st4(Yo + oy + d.yoff[t0 + j], acc[0][j] * scale, acc[1][j] * scale,
-                            acc[2][j] * scale, acc[3][j] * scale);
+            for (int j = 0; j < 4; ++j) {
+                if (t0 + j >= d.nt) break;
+                st4(ys + (t0 + j) * RS + 4 * pg, acc[0][j] * scale, acc[1][j] * scale,
+                    acc[2][j] * scale, acc[3][j] * scale);
 #pragma unroll
-                        for (int i = 0; i < 4; ++i) mx = mx > acc[i][j] ? mx : acc[i][j];
-                    }
+                for (int i = 0; i < 4; ++i) mx = mx > acc[i][j] ? mx : acc[i][j];
+            }
+            __syncthreads();
+            T *Yt = Yo + __ldg(ty + (int)crem * AD_P);
+            const int32_t *cry = d.tab + d.cyo;
+            const uint2 *csy = (const uint2 *)(d.tab + d.cyo + nqy);
+            for (int q = tid; q < nqy; q += 256) {
+                const uint2 w = __ldg(csy + q);
+                st4(Yt + __ldg(cry + q), ys[w.x & 0xffffu], ys[w.x >> 16], ys[w.y & 0xffffu],
+                    ys[w.y >> 16]);
+            }
+        } else if (ym == 1) {
+            if (j0 < nin) {
+                const int oy = __ldg(ty + j0);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (t0 + j >= d.nt) break;
+                    st4(Yo + oy + d.yoff[t0 + j], acc[0][j] * scale, acc[1][j] * scale,
+                        acc[2][j] * scale, acc[3][j] * scale);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) mx = mx > acc[i][j] ? mx : acc[i][j];
                 }
-            } else if (ym == 2) {
-                if (t0 < d.nt) {
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        if (j0 + i >= nin) break;
-                        st4(Yo + __ldg(ty + j0 + i) + d.yoff[t0], acc[i][0] * scale,
-                            acc[i][1] * scale, acc[i][2] * scale, acc[i][3] * scale);
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) mx = mx > acc[i][j] ? mx : acc[i][j];
-                    }
-                }
-            } else {
+            }
+        } else if (ym == 2) {
+            if (t0 < d.nt) {
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     if (j0 + i >= nin) break;
-                    const int oy = __ldg(ty + j0 + i);
+                    st4(Yo + __ldg(ty + j0 + i) + d.yoff[t0], acc[i][0] * scale,
+                        acc[i][1] * scale, acc[i][2] * scale, acc[i][3] * scale);
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        if (t0 + j >= d.nt) break;
-                        Yo[oy + d.yoff[t0 + j]] = acc[i][j] * scale;
-                        mx = mx > acc[i][j] ? mx : acc[i][j];
-                    }
+                    for (int j = 0; j < 4; ++j) mx = mx > acc[i][j] ? mx : acc[i][j];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (j0 + i >= nin) break;
+                const int oy = __ldg(ty + j0 + i);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (t0 + j >= d.nt) break;
+                    Yo[oy + d.yoff[t0 + j]] = acc[i][j] * scale;
+                    mx = mx > acc[i][j] ? mx : acc[i][j];
                 }
             }
         }
@@ -314,20 +374,30 @@ __global__ void __launch_bounds__(256) k_absorb_dense(const __grid_constant__ AD
 constexpr int RD_P = 64;    // positions per tile
 constexpr int RD_S = 3;     // tile buffers
 
+// Per tile buffer: the [64 rows: X s, then Z t][RD_P + pad] tile and, for
+// each operand copied as planned chunks (chunk mode), a staging area of its
+// 32 x RD_P entries in memory order.  The final per-group sums [4][1024]
+// reuse the buffers.
 template <typename T>
-__host__ __device__ constexpr size_t reduce_dense_smem() {
-    // tiles [RD_S][64 rows: X s, then Z t][RD_P + pad]; the final per-group
-    // sums [4][1024] reuse them
-    return (size_t)RD_S * 64 * (RD_P + ad_pad<T>()) * sizeof(T);
+__host__ __device__ constexpr int rd_tile() {
+    return 64 * (RD_P + ad_pad<T>());
+}
+template <typename T>
+__host__ __device__ inline size_t reduce_dense_smem(int nchunked) {
+    return (size_t)RD_S * (rd_tile<T>() + nchunked * 32 * RD_P) * sizeof(T);
 }
 
-// vm bit 0: four consecutive positions of X per copy, bit 1: the same for Z.
+// Operand modes (X in bits 0-1, Z in bits 2-3): 0 one entry per copy,
+// 1 four consecutive positions per copy, 3 the tile's 16-byte chunks in
+// memory order (planned table), scattered into the tile's rows.
 template <typename T>
-__global__ void __launch_bounds__(256) k_reduce_dense(const __grid_constant__ RDesc d, int vm,
+__global__ void __launch_bounds__(256) k_reduce_dense(const __grid_constant__ RDesc d, int modes,
                                                       int64_t chunk, int nchunks, T *part) {
     extern __shared__ __align__(16) unsigned char smraw[];
     constexpr int RR = RD_P + ad_pad<T>();
-    constexpr int TB = 64 * RR;
+    const int mx_ = modes & 3, mz_ = (modes >> 2) & 3;
+    const int nchunked = (mx_ == 3) + (mz_ == 3);
+    const int TB = rd_tile<T>() + nchunked * 32 * RD_P;   // one buffer
     T *Ts = (T *)smraw;
     const int tid = threadIdx.x;
     const int nin = (int)d.nin;
@@ -348,6 +418,8 @@ __global__ void __launch_bounds__(256) k_reduce_dense(const __grid_constant__ RD
     const int lcper = log2_if_pow2(cper);
     const T *X = (const T *)d.X, *Z = (const T *)d.Z;
     const uint32_t ts0 = (uint32_t)__cvta_generic_to_shared(Ts);
+    // staging of operand h (chunk mode) inside a buffer, after the tile
+    auto stage_off = [&](int h) { return rd_tile<T>() + (h == 1 && mx_ == 3 ? 32 * RD_P : 0); };
     auto issue = [&](int k, int b) {
         if (k < nk) {
             int64_t crem;
@@ -362,13 +434,19 @@ __global__ void __launch_bounds__(256) k_reduce_dense(const __grid_constant__ RD
                 const T *base = h ? Z + cbz : X + cbx;
                 const int *tab = h ? tz : tx;
                 const int nv = h ? d.nt : d.ns;
-                const bool v4 = (vm >> h) & 1;
-                if (v4) {
+                const int md = h ? mz_ : mx_;
+                if (md == 3) {
+                    const T *bt = base + __ldg(tab + j0);
+                    const int32_t *crel = d.tab + (h ? d.czo : d.cxo);
+                    const uint32_t st = sb + (uint32_t)(stage_off(h) * sizeof(T));
+                    for (int q = tid; q < nv * (RD_P / 4); q += 256)
+                        cp_async4<T>(st + (uint32_t)(4 * q * sizeof(T)), bt + __ldg(crel + q), true);
+                } else if (md == 1) {
                     for (int e = tid; e < 32 * (RD_P / 4); e += 256) {
                         const int v = e / (RD_P / 4), p = (e % (RD_P / 4)) * 4;
                         const int j = j0 + p;
                         const bool ok = v < nv && j < nin;
-                        const int64_t off = h ? d.zoff[v < 32 ? v : 0] : d.xoff[v < 32 ? v : 0];
+                        const int64_t off = h ? d.zoff[v] : d.xoff[v];
                         cp_async4<T>(sb + (uint32_t)(((32 * h + v) * RR + p) * sizeof(T)),
                                      ok ? base + __ldg(tab + j) + off : base, ok);
                     }
@@ -401,7 +479,22 @@ __global__ void __launch_bounds__(256) k_reduce_dense(const __grid_constant__ RD
         cp_async_wait<1>();
         __syncthreads();
         issue(k + 2, b == 0 ? 2 : b - 1);
-        const T *tb = Ts + b * TB;
+        T *tb = Ts + b * TB;
+        if (nchunked) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if ((h ? mz_ : mx_) != 3) continue;
+                const int nq = (h ? d.nt : d.ns) * (RD_P / 4);
+                const uint2 *cs = (const uint2 *)(d.tab + (h ? d.czo : d.cxo) + nq);
+                const T *st = tb + stage_off(h);
+                for (int q = tid; q < nq; q += 256) {
+                    T v[4];
+                    ld4(st + 4 * q, v);
+                    scatter4(tb, __ldg(cs + q), v);
+                }
+            }
+            __syncthreads();
+        }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int p = 16 * pq + 4 * q;

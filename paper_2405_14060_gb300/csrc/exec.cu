@@ -668,12 +668,16 @@ static bool make_absorb(const std::vector<int> &card, const Labels &lx, bool bx,
     std::set<int> sx(lx.begin(), lx.end()), sw(lw.begin(), lw.end()), sy(ly.begin(), ly.end());
     Labels R, T, S;
     for (int v : ly) (sx.count(v) ? R : T).push_back(v);
-    if (sorder) S = *sorder;
+    // summed combinations in the elimination order where an argmax records a
+    // flat index over them; otherwise W-only labels first, then X's summed
+    // labels in X's order (X's fastest summed labels enumerate fastest, so
+    // their offsets run contiguously where X stores them so)
+    if (sorder && argmax) S = *sorder;
     else {
-        for (int v : lx)
-            if (!sy.count(v)) S.push_back(v);
         for (int v : lw)
             if (!sy.count(v) && !sx.count(v)) S.push_back(v);
+        for (int v : lx)
+            if (!sy.count(v)) S.push_back(v);
     }
     if (!combo_offsets(card, S, lx, sx, lw, sw, AMAX, d.ns, d.xoff, d.wso)) { absorb_reject = "summed combinations"; return false; }
     if (!combo_offsets(card, T, ly, sy, lw, sw, AMAX, d.nt, d.yoff, d.wto)) { absorb_reject = "new combinations"; return false; }
@@ -1041,7 +1045,53 @@ static bool to_micro(const CDesc &d, const char *arena, int esz, const unsigned 
 }
 
 // Inner offset tables of the streaming kernels (computed once per node).
-static void absorb_table(const ADesc &d, std::vector<int32_t> &out) {
+// Chunk table of one operand tile of a dense kernel (dense_impl.cuh): tiles
+// are P consecutive inner positions; entry (p, v) of a tile sits at
+// pos[c P + p] + voff[v] from the operand's base, which must be the tile's
+// base pos[c P] (a multiple of 4) plus a pattern that is the same for every
+// tile c.  Sorted by offset, the pattern's entries must form whole, aligned
+// quads of consecutive entries.  Appends the quads' offsets [nq] and, per
+// quad, the shared-memory slots (row0 + v) * RS + p of its four entries
+// (16-bit, [nq][4]) to `out` (even-aligned) and returns the table position,
+// or -1 when the pattern does not chunk.
+template <typename O>
+static int dense_chunks(const std::vector<int64_t> &pos, int P, const O *voff, int nv, int RS,
+                        int row0, bool base4, std::vector<int32_t> &out) {
+    const int64_t nin = (int64_t)pos.size();
+    if (!base4 || nin % P || nv < 1) return -1;
+    for (int64_t c = 0; c < nin; c += P) {
+        if (pos[c] % 4) return -1;
+        for (int p = 0; p < P; ++p)
+            if (pos[c + p] - pos[c] != pos[p] - pos[0]) return -1;
+    }
+    struct E { int64_t off; int slot; };
+    std::vector<E> es;
+    es.reserve((size_t)P * nv);
+    for (int v = 0; v < nv; ++v) {
+        for (int p = 0; p < P; ++p)
+            es.push_back({pos[p] - pos[0] + (int64_t)voff[v], (row0 + v) * RS + p});
+    }
+    std::sort(es.begin(), es.end(), [](const E &a, const E &b) { return a.off < b.off; });
+    if (es.size() % 4) return -1;
+    const size_t nq = es.size() / 4;
+    for (size_t q = 0; q < nq; ++q) {
+        const int64_t o = es[4 * q].off;
+        if (o % 4 || o >= (1LL << 31)) return -1;
+        for (int i = 1; i < 4; ++i)
+            if (es[4 * q + i].off != o + i) return -1;
+    }
+    if (out.size() % 2) out.push_back(0);
+    const int at = (int)out.size();
+    out.resize(out.size() + 3 * nq, 0);
+    uint16_t *sl = (uint16_t *)(out.data() + at + nq);
+    for (size_t q = 0; q < nq; ++q) {
+        out[at + q] = (int32_t)es[4 * q].off;
+        for (int i = 0; i < 4; ++i) sl[4 * q + i] = (uint16_t)es[4 * q + i].slot;
+    }
+    return at;
+}
+
+static void absorb_table(ADesc &d, int esz, std::vector<int32_t> &out) {
     const int nin = (int)d.nin, nod = d.nrd - d.nin_d;
     out.assign((size_t)4 * nin + d.nsh, 0);
     for (int i = 0; i < nin; ++i) {
@@ -1070,9 +1120,33 @@ static void absorb_table(const ADesc &d, std::vector<int32_t> &out) {
         }
         out[4 * nin + c] = (int32_t)w0;
     }
+    // chunked tile copies of the dense absorb
+    d.cx = d.cy = 0;
+    if (absorb_dense_form_host(d)) {
+        const int P = 128, RS = P + 16 / esz;
+        const int nod2 = d.nrd - d.nin_d;
+        auto base4 = [&](const int64_t *st, int64_t bs, const void *ptr) {
+            if (bs % 4 || ((uintptr_t)ptr & 15)) return false;
+            for (int k = 0; k < nod2; ++k)
+                if (st[k] % 4) return false;
+            return true;
+        };
+        std::vector<int64_t> px(out.begin(), out.begin() + nin),
+            py(out.begin() + nin, out.begin() + 2 * nin);
+        int at = dense_chunks(px, P, d.xoff, d.ns, RS, 0, base4(d.rsx, d.bsx, d.X), out);
+        if (at >= 0) {
+            d.cx = 1;
+            d.cxo = at;
+        }
+        at = dense_chunks(py, P, d.yoff, d.nt, RS, 0, base4(d.rsy, d.bsy, d.Y), out);
+        if (at >= 0) {
+            d.cy = 1;
+            d.cyo = at;
+        }
+    }
 }
 
-static void reduce_table(const RDesc &d, std::vector<int32_t> &out) {
+static void reduce_table(RDesc &d, int esz, std::vector<int32_t> &out) {
     const int nin = (int)d.nin, nod = d.nmd - d.nin_d;
     out.assign((size_t)2 * nin, 0);
     for (int i = 0; i < nin; ++i) {
@@ -1085,6 +1159,31 @@ static void reduce_table(const RDesc &d, std::vector<int32_t> &out) {
         }
         out[i] = (int32_t)x0;
         out[nin + i] = (int32_t)z0;
+    }
+    // chunked tile copies of the dense reduce
+    d.cx = d.cz = 0;
+    if (reduce_dense_describe(d) >= 0) {
+        const int P = 64, RR = P + 16 / esz;
+        auto base4 = [&](const int64_t *ms, const int64_t *gs, int64_t bs, const void *ptr) {
+            if (bs % 4 || ((uintptr_t)ptr & 15)) return false;
+            for (int k = 0; k < nod; ++k)
+                if (ms[k] % 4) return false;
+            for (int k = 0; k < d.ngd; ++k)
+                if (gs[k] % 4) return false;
+            return true;
+        };
+        std::vector<int64_t> px(out.begin(), out.begin() + nin),
+            pz(out.begin() + nin, out.begin() + 2 * nin);
+        int at = dense_chunks(px, P, d.xoff, d.ns, RR, 0, base4(d.msx, d.gsx, d.bsx, d.X), out);
+        if (at >= 0) {
+            d.cx = 1;
+            d.cxo = at;
+        }
+        at = dense_chunks(pz, P, d.zoff, d.nt, RR, 32, base4(d.msz2, d.gsz2, d.bsz, d.Z), out);
+        if (at >= 0) {
+            d.cz = 1;
+            d.czo = at;
+        }
     }
 }
 
@@ -1106,6 +1205,11 @@ static void trace_program(const Program &P) {
                 for (int k = 0; k < a.ns && k < 8; ++k) fprintf(stderr, ",%d", a.xoff[k]);
                 fprintf(stderr, " yoff");
                 for (int k = 0; k < a.nt && k < 8; ++k) fprintf(stderr, ",%d", a.yoff[k]);
+                {
+                    int xm, ym;
+                    absorb_dense_describe(a, xm, ym);
+                    if (xm >= 0) fprintf(stderr, " dense x%d y%d", xm, ym);
+                }
                 fprintf(stderr, " rdims");
                 for (int k = 0; k < a.nrd; ++k)
                     fprintf(stderr, ",%d:%lld/%lld/%lld", a.rsz[k], (long long)a.rsx[k],
@@ -1119,6 +1223,7 @@ static void trace_program(const Program &P) {
                 for (int k = 0; k < r.ns && k < 8; ++k) fprintf(stderr, ",%lld", (long long)r.xoff[k]);
                 fprintf(stderr, " zoff");
                 for (int k = 0; k < r.nt && k < 8; ++k) fprintf(stderr, ",%lld", (long long)r.zoff[k]);
+                if (reduce_dense_describe(r) >= 0) fprintf(stderr, " dense v%d", reduce_dense_describe(r));
                 fprintf(stderr, " mdims");
                 for (int k = 0; k < r.nmd; ++k)
                     fprintf(stderr, ",%d:%lld/%lld", r.msz[k], (long long)r.msx[k],
@@ -1802,7 +1907,6 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                 st.bd.tc = 0;
             }
         }
-    trace_program(P);
     // inner offset tables of the streaming steps, one device buffer
     {
         std::vector<int32_t> all, t;
@@ -1821,10 +1925,11 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                     }
                     continue;
                 }
-                if (st.kind == 2) absorb_table(st.ad, t);
-                else if (st.kind == 3) reduce_table(st.rd, t);
+                if (st.kind == 2) absorb_table(st.ad, P.esz, t);
+                else if (st.kind == 3) reduce_table(st.rd, P.esz, t);
                 else if (st.kind == 4) t = st.btab;
                 else continue;
+                all.resize((all.size() + 3) & ~(size_t)3);   // 16-byte aligned
                 where.push_back({&st, all.size()});
                 all.insert(all.end(), t.begin(), t.end());
             }
@@ -1848,6 +1953,7 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
             for (auto &w : pwhere) w.first->tl.ttab = dt + w.second;
         }
     }
+    trace_program(P);
     // GEMM workspaces (one set per lane that runs GEMM steps), then patch
     // the steps' workspace pointers
     {

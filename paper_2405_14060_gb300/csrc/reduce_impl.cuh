@@ -446,22 +446,31 @@ static int reduce_dense_vm(const RDesc &d) {
            (ok(d.Z, d.bsz, d.msz2, d.gsz2, d.zoff, d.nt) ? 2 : 0);
 }
 
+// Operand modes of k_reduce_dense: four positions per copy where possible,
+// else the planned chunk table, else one entry per copy.
+static int reduce_dense_modes(const RDesc &d) {
+    const int vm = reduce_dense_vm(d);
+    const int mx = (vm & 1) ? 1 : d.cx ? 3 : 0;
+    const int mz = (vm & 2) ? 1 : d.cz ? 3 : 0;
+    return mx | (mz << 2);
+}
+
 template <typename T>
 static void reduce_dense_go(const RDesc &d, void *scratch, cudaStream_t st) {
     const int64_t groups = d.ng * d.nbeta;
     int64_t chunk;
     int nchunks;
     reduce_dense_shape(d, chunk, nchunks);
-    constexpr size_t smem = reduce_dense_smem<T>();
+    const int modes = reduce_dense_modes(d);
+    const size_t smem = reduce_dense_smem<T>(((modes & 3) == 3) + (((modes >> 2) & 3) == 3));
     static std::once_flag once;
     std::call_once(once, [] {
         cudaFuncSetAttribute(k_reduce_dense<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+                             (int)reduce_dense_smem<T>(2));
     });
     dim3 grid((unsigned)nchunks, (unsigned)std::min<int64_t>(groups, 65535),
               (unsigned)((groups + 65534) / 65535));
-    k_reduce_dense<T><<<grid, 256, smem, st>>>(d, reduce_dense_vm(d), chunk, nchunks,
-                                               (T *)scratch);
+    k_reduce_dense<T><<<grid, 256, smem, st>>>(d, modes, chunk, nchunks, (T *)scratch);
 }
 
 #ifdef TN_STREAM_HOST_DEFS
@@ -539,6 +548,7 @@ void launch_reduce(const RDesc &d, void *scratch, cudaStream_t st) {
 }
 
 #ifdef TN_STREAM_HOST_DEFS
+int reduce_dense_describe(const RDesc &d) { return reduce_dense_form(d) ? reduce_dense_modes(d) : -1; }
 int reduce_launches(const RDesc &d) {
     return reduce_dense_form(d) ? 1 : (int)reduce_pieces(d, 4).size();
 }

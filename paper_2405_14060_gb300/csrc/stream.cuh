@@ -37,6 +37,10 @@ struct ADesc {
     int nsh;                          // combinations of the labels W shares with X and Y
     int32_t rshc[MAXD];               // per R dim: stride in that combination index (0: not in W)
     int bps;                          // blocks per SM of the launch (0: the kernel's default)
+    // dense kernel (dense_impl.cuh): chunk tables of X's and Y's tiles in tab
+    // (positions; used when cx / cy are set)
+    int cx, cy;
+    int32_t cxo, cyo;
 };
 
 // Reduce: O[g, s, t] = sum_m X[g, m, s] Z[g, m, t]
@@ -64,6 +68,9 @@ struct RDesc {
     unsigned long long *mxo;
     const int32_t *tab;               // inner offsets: X [nin], Z [nin] (device)
     unsigned int *cnt;                // per group: blocks done (zero between launches)
+    // dense kernel (dense_impl.cuh): chunk tables of X's and Z's tiles in tab
+    int cx, cz;
+    int32_t cxo, czo;
 };
 
 template <typename T>
@@ -74,5 +81,9 @@ void launch_reduce(const RDesc &d, void *scratch, cudaStream_t st);
 int reduce_launches(const RDesc &d);
 // Does the reduce run as k_reduce_vec (16-byte vector loads)?
 bool reduce_vector_form(const RDesc &d, int elem_bytes);
+// Plan trace: the dense kernels' load / store modes (-1: not the dense form).
+void absorb_dense_describe(const ADesc &d, int &xm, int &ym);
+bool absorb_dense_form_host(const ADesc &d);
+int reduce_dense_describe(const RDesc &d);
 
 }  // namespace tn

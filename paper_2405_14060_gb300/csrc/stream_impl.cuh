@@ -383,12 +383,15 @@ static DenseModes absorb_dense_modes(const ADesc &d) {
         if (pos4 && d.rsy[L] == 1 && strides4(d.rsy, L) && offs4(d.yoff, d.nt)) m.ym = 1;
         else if (strides4(d.rsy, -1) && quads(d.yoff, d.nt) && offs4(d.yoff, d.nt)) m.ym = 2;
     }
+    // otherwise the planned chunk tables, where the layout allows them
+    if (m.xm == 0 && d.cx) m.xm = 3;
+    if (m.ym == 0 && d.cy) m.ym = 3;
     return m;
 }
 
 template <typename T, int XM>
 static void absorb_dense_go(const ADesc &d, int ym, cudaStream_t st) {
-    constexpr size_t smem = absorb_dense_smem<T>();
+    constexpr size_t smem = absorb_dense_smem<T, XM>();
     static std::once_flag once;
     std::call_once(once, [] {
         cudaFuncSetAttribute(k_absorb_dense<T, XM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -407,6 +410,17 @@ static bool absorb_dense_form(const ADesc &d) {
     return pow2ceil(d.ns) * pow2ceil(d.nt) > 256;
 }
 
+#ifdef TN_STREAM_HOST_DEFS
+bool absorb_dense_form_host(const ADesc &d) { return absorb_dense_form(d); }
+void absorb_dense_describe(const ADesc &d, int &xm, int &ym) {
+    xm = ym = -1;
+    if (!absorb_dense_form(d)) return;
+    const DenseModes m = absorb_dense_modes(d);
+    xm = m.xm;
+    ym = m.ym;
+}
+#endif
+
 template <typename T>
 void launch_absorb(const ADesc &d0, int semiring, cudaStream_t st) {
     if (d0.nr * d0.nbeta == 0) return;
@@ -416,6 +430,7 @@ void launch_absorb(const ADesc &d0, int semiring, cudaStream_t st) {
         const DenseModes m = absorb_dense_modes(d);
         if (m.xm == 1) absorb_dense_go<T, 1>(d, m.ym, st);
         else if (m.xm == 2) absorb_dense_go<T, 2>(d, m.ym, st);
+        else if (m.xm == 3) absorb_dense_go<T, 3>(d, m.ym, st);
         else absorb_dense_go<T, 0>(d, m.ym, st);
         return;
     }
