@@ -167,7 +167,7 @@ __device__ __forceinline__ void scatter4(T *dst, uint2 w, const T (&v)[4]) {
 // combinations per store (all from registers), 3 through shared memory as
 // the tile's chunks in memory order (chunk table at d.cyo).
 template <typename T, int XM>
-__global__ void __launch_bounds__(256) k_absorb_dense(const __grid_constant__ ADesc d, int ym) {
+__global__ void __launch_bounds__(256, 3) k_absorb_dense(const __grid_constant__ ADesc d, int ym) {
     extern __shared__ __align__(16) unsigned char smraw[];
     constexpr int PAD = ad_pad<T>();
     constexpr int WR = 32 + PAD;                       // W row: [s][t]
@@ -202,6 +202,20 @@ __global__ void __launch_bounds__(256) k_absorb_dense(const __grid_constant__ AD
     const T *X = (const T *)d.X + beta * d.bsx;
     T *Y = (T *)d.Y + beta * d.bsy;
     const uint32_t xs0 = (uint32_t)__cvta_generic_to_shared(Xs);
+    // X chunk mode: this thread's chunks q = tid + 256 r are the same in
+    // every tile, so their offsets and slots stay in registers
+    int32_t xrel[4];
+    uint2 xsl[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int q = tid + 256 * r;
+        xrel[r] = 0;
+        xsl[r] = make_uint2(0u, 0u);
+        if (XM == 3 && q < nqx) {
+            xrel[r] = __ldg(d.tab + d.cxo + q);
+            xsl[r] = __ldg((const uint2 *)(d.tab + d.cxo + nqx) + q);
+        }
+    }
     // copies of this block's k-th tile into buffer b (an empty group past the end)
     auto issue = [&](int64_t k, int b) {
         if (k < mine) {
@@ -214,9 +228,12 @@ __global__ void __launch_bounds__(256) k_absorb_dense(const __grid_constant__ AD
             const uint32_t sb = xs0 + (uint32_t)(b * TB * sizeof(T));
             if (XM == 3) {
                 const T *Xt = Xo + __ldg(tx + j0);
-                const int32_t *crel = d.tab + d.cxo;
-                for (int q = tid; q < nqx; q += 256)
-                    cp_async4<T>(sb + (uint32_t)(4 * q * sizeof(T)), Xt + __ldg(crel + q), true);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int q = tid + 256 * r;
+                    if (q < nqx)
+                        cp_async4<T>(sb + (uint32_t)(4 * q * sizeof(T)), Xt + xrel[r], true);
+                }
             } else if (XM == 1) {
                 // 32 rows x 32 quads of positions
                 for (int e = tid; e < 32 * (AD_P / 4); e += 256) {
@@ -260,11 +277,14 @@ __global__ void __launch_bounds__(256) k_absorb_dense(const __grid_constant__ AD
         T *tb = Xs + b * TB;
         const T *xb = tb;
         if (XM == 3) {
-            const uint2 *cs = (const uint2 *)(d.tab + d.cxo + nqx);
-            for (int q = tid; q < nqx; q += 256) {
-                T v[4];
-                ld4(tb + 4 * q, v);
-                scatter4(Xc, __ldg(cs + q), v);
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int q = tid + 256 * r;
+                if (q < nqx) {
+                    T v[4];
+                    ld4(tb + 4 * q, v);
+                    scatter4(Xc, xsl[r], v);
+                }
             }
             __syncthreads();
             xb = Xc;
@@ -420,6 +440,23 @@ __global__ void __launch_bounds__(256) k_reduce_dense(const __grid_constant__ RD
     const uint32_t ts0 = (uint32_t)__cvta_generic_to_shared(Ts);
     // staging of operand h (chunk mode) inside a buffer, after the tile
     auto stage_off = [&](int h) { return rd_tile<T>() + (h == 1 && mx_ == 3 ? 32 * RD_P : 0); };
+    // chunk modes: this thread's chunks q = tid + 256 r (r < 2) of each operand,
+    // the same in every tile, kept in registers
+    int32_t crel[2][2];
+    uint2 csl[2][2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int nq = (h ? d.nt : d.ns) * (RD_P / 4), q = tid + 256 * r;
+            const int32_t at = h ? d.czo : d.cxo;
+            crel[h][r] = 0;
+            csl[h][r] = make_uint2(0u, 0u);
+            if ((h ? mz_ : mx_) == 3 && q < nq) {
+                crel[h][r] = __ldg(d.tab + at + q);
+                csl[h][r] = __ldg((const uint2 *)(d.tab + at + nq) + q);
+            }
+        }
     auto issue = [&](int k, int b) {
         if (k < nk) {
             int64_t crem;
@@ -437,10 +474,13 @@ __global__ void __launch_bounds__(256) k_reduce_dense(const __grid_constant__ RD
                 const int md = h ? mz_ : mx_;
                 if (md == 3) {
                     const T *bt = base + __ldg(tab + j0);
-                    const int32_t *crel = d.tab + (h ? d.czo : d.cxo);
                     const uint32_t st = sb + (uint32_t)(stage_off(h) * sizeof(T));
-                    for (int q = tid; q < nv * (RD_P / 4); q += 256)
-                        cp_async4<T>(st + (uint32_t)(4 * q * sizeof(T)), bt + __ldg(crel + q), true);
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        const int q = tid + 256 * r;
+                        if (q < nv * (RD_P / 4))
+                            cp_async4<T>(st + (uint32_t)(4 * q * sizeof(T)), bt + crel[h][r], true);
+                    }
                 } else if (md == 1) {
                     for (int e = tid; e < 32 * (RD_P / 4); e += 256) {
                         const int v = e / (RD_P / 4), p = (e % (RD_P / 4)) * 4;
@@ -485,12 +525,15 @@ __global__ void __launch_bounds__(256) k_reduce_dense(const __grid_constant__ RD
             for (int h = 0; h < 2; ++h) {
                 if ((h ? mz_ : mx_) != 3) continue;
                 const int nq = (h ? d.nt : d.ns) * (RD_P / 4);
-                const uint2 *cs = (const uint2 *)(d.tab + (h ? d.czo : d.cxo) + nq);
                 const T *st = tb + stage_off(h);
-                for (int q = tid; q < nq; q += 256) {
-                    T v[4];
-                    ld4(st + 4 * q, v);
-                    scatter4(tb, __ldg(cs + q), v);
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const int q = tid + 256 * r;
+                    if (q < nq) {
+                        T v[4];
+                        ld4(st + 4 * q, v);
+                        scatter4(tb, csl[h][r], v);
+                    }
                 }
             }
             __syncthreads();

@@ -114,7 +114,7 @@ __device__ __forceinline__ void store_conv(void *out, int64_t i, TI x) {
 // (t.vec outputs per 16-byte store, their shared-memory slots read as one
 // vector of 16-bit integers).
 template <typename TI, int OT>
-__global__ void __launch_bounds__(256) k_permute_tiled(const __grid_constant__ PDesc p,
+__global__ void __launch_bounds__(256, 4) k_permute_tiled(const __grid_constant__ PDesc p,
                                                        int64_t per_item) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ int64_t sbase[4][3];   // per tile (mod 4): input base, output base, item
