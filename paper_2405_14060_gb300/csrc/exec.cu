@@ -1669,6 +1669,23 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
         tn_status fs = fwd_step(id, fptr(id), P.fsteps, false, true);
         if (fs) return fs;
     }
+    // label order of each adjoint tensor: the node's own, except where a
+    // GEMM-form adjoint step can write its result straight from the GEMM
+    // ([batch][rows][cols], no scatter pass); leaves and micro subtrees keep
+    // the node order (marginals and the micro kernel read them so)
+    std::vector<Labels> adjlab(NN);
+    for (int i = 0; i < NN; ++i) adjlab[i] = pl.node[i].labels;
+    auto alab = [&](int i) -> const Labels & { return adjlab[i]; };
+    auto gemm_adj_layout = [&](int child, const Labels &bt, const Labels &rows,
+                               const Labels &cols, bool xbeta, bool ybeta) {
+        if (child < n || P.micro[child]) return;
+        const int bpos = xbeta && ybeta ? 1 : xbeta ? 2 : ybeta ? 3 : 0;
+        if (bpos == 3 || (bpos == 2 && !bt.empty())) return;   // batch label outermost
+        Labels l(bt);
+        l.insert(l.end(), rows.begin(), rows.end());
+        l.insert(l.end(), cols.begin(), cols.end());
+        adjlab[child] = l;
+    };
     if (backward) {
         for (int id = NN - 1; id >= n; --id) {
             if (P.micro[id]) continue;
@@ -1684,14 +1701,15 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
             double flops = 2.0 * nd.muladds * items;
             if (nd.gemm) {
                 const Node &xa = pl.node[nd.ga], &xb = pl.node[nd.gb];
-                Opnd Cb{&nd.labels, (bool)P.adj_beta[id], P.adj[id].per, cbar, P.mx + P.adj[id].mx};
+                Opnd Cb{&alab(id), (bool)P.adj_beta[id], P.adj[id].per, cbar, P.mx + P.adj[id].mx};
                 Opnd A{&xa.labels, xa.beta, P.fwd[nd.ga].per, bfptr(nd.ga), P.mx + P.fwd[nd.ga].mx};
                 Opnd Bo{&xb.labels, xb.beta, P.fwd[nd.gb].per, bfptr(nd.gb), P.mx + P.fwd[nd.gb].mx};
                 if (P.need_adj[nd.ga]) {
                     // Abar[bt, m, k] = sum_n Cbar[bt, m, n] B[bt, k, n]
+                    gemm_adj_layout(nd.ga, nd.gbt, nd.gm, nd.elim, P.adj_beta[id], xb.beta);
                     double bytes = (double)P.esz * (P.adj[id].elems + P.fwd[nd.gb].elems +
                                                     P.adj[nd.ga].elems);
-                    err = add_gemm(P.bsteps, Cb, Bo, nd.gbt, nd.gm, nd.elim, nd.gn, xa.labels,
+                    err = add_gemm(P.bsteps, Cb, Bo, nd.gbt, nd.gm, nd.elim, nd.gn, alab(nd.ga),
                                    P.adj_beta[nd.ga], aptr(nd.ga), P.mx + P.adj[nd.ga].mx, flops,
                                    bytes);
                     if (!err.empty()) return fail(TN_E_UNSUPPORTED, err);
@@ -1700,9 +1718,10 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                 }
                 if (P.need_adj[nd.gb]) {
                     // Bbar[bt, k, n] = sum_m A[bt, m, k] Cbar[bt, m, n]
+                    gemm_adj_layout(nd.gb, nd.gbt, nd.elim, nd.gn, xa.beta, P.adj_beta[id]);
                     double bytes = (double)P.esz * (P.fwd[nd.ga].elems + P.adj[id].elems +
                                                     P.adj[nd.gb].elems);
-                    err = add_gemm(P.bsteps, A, Cb, nd.gbt, nd.elim, nd.gn, nd.gm, xb.labels,
+                    err = add_gemm(P.bsteps, A, Cb, nd.gbt, nd.elim, nd.gn, nd.gm, alab(nd.gb),
                                    P.adj_beta[nd.gb], aptr(nd.gb), P.mx + P.adj[nd.gb].mx, flops,
                                    bytes);
                     if (!err.empty()) return fail(TN_E_UNSUPPORTED, err);
@@ -1716,28 +1735,28 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                 Step st;
                 st.flops = flops;
                 st.bytes = (double)P.esz * (P.adj[id].elems + P.fwd[nd.b].elems + P.adj[nd.a].elems);
-                if (make_absorb(net.card, nd.labels, P.adj_beta[id], P.adj[id].per, cbar,
+                if (make_absorb(net.card, alab(id), P.adj_beta[id], P.adj[id].per, cbar,
                                 P.mx + P.adj[id].mx, nb.labels, nb.beta, P.fwd[nd.b].per,
-                                bfptr(nd.b), P.mx + P.fwd[nd.b].mx, na.labels, P.adj_beta[nd.a],
+                                bfptr(nd.b), P.mx + P.fwd[nd.b].mx, alab(nd.a), P.adj_beta[nd.a],
                                 P.adj[nd.a].per, aptr(nd.a), P.mx + P.adj[nd.a].mx, nullptr, nbeta,
                                 nullptr, st.ad, true) ||
                     make_absorb(net.card, nb.labels, nb.beta, P.fwd[nd.b].per, bfptr(nd.b),
-                                P.mx + P.fwd[nd.b].mx, nd.labels, P.adj_beta[id], P.adj[id].per,
-                                cbar, P.mx + P.adj[id].mx, na.labels, P.adj_beta[nd.a],
+                                P.mx + P.fwd[nd.b].mx, alab(id), P.adj_beta[id], P.adj[id].per,
+                                cbar, P.mx + P.adj[id].mx, alab(nd.a), P.adj_beta[nd.a],
                                 P.adj[nd.a].per, aptr(nd.a), P.mx + P.adj[nd.a].mx, nullptr, nbeta,
                                 nullptr, st.ad, true)) {
                     st.kind = 2;
-                } else if (make_bgemm(net.card, nd.labels, P.adj_beta[id], P.adj[id].per, cbar,
+                } else if (make_bgemm(net.card, alab(id), P.adj_beta[id], P.adj[id].per, cbar,
                                       P.mx + P.adj[id].mx, nb.labels, nb.beta, P.fwd[nd.b].per,
-                                      bfptr(nd.b), P.mx + P.fwd[nd.b].mx, na.labels,
+                                      bfptr(nd.b), P.mx + P.fwd[nd.b].mx, alab(nd.a),
                                       P.adj_beta[nd.a], P.adj[nd.a].per, aptr(nd.a),
                                       P.mx + P.adj[nd.a].mx, nbeta, P.esz, st.bd, st.btab)) {
                     st.kind = 4;
                     scratch = std::max(scratch, bgemm_scratch_bytes(st.bd, P.esz));
                 } else {
-                    err = make_desc(net.card, nd.labels, P.adj_beta[id], P.adj[id].per, cbar,
+                    err = make_desc(net.card, alab(id), P.adj_beta[id], P.adj[id].per, cbar,
                                     P.mx + P.adj[id].mx, nb.labels, nb.beta, P.fwd[nd.b].per,
-                                    bfptr(nd.b), P.mx + P.fwd[nd.b].mx, na.labels, P.adj_beta[nd.a],
+                                    bfptr(nd.b), P.mx + P.fwd[nd.b].mx, alab(nd.a), P.adj_beta[nd.a],
                                     aptr(nd.a), P.mx + P.adj[nd.a].mx, nullptr, nbeta, nullptr,
                                     st.d);
                     if (!err.empty()) return fail(TN_E_UNSUPPORTED, err);
@@ -1756,34 +1775,34 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                 st.bytes = (double)P.esz * (P.fwd[nd.a].elems + P.adj[id].elems + P.adj[nd.b].elems);
                 if (P.adj[nd.b].elems >= (1 << 16) &&
                     (make_absorb(net.card, na.labels, na.beta, P.fwd[nd.a].per, bfptr(nd.a),
-                                 P.mx + P.fwd[nd.a].mx, nd.labels, P.adj_beta[id], P.adj[id].per,
-                                 cbar, P.mx + P.adj[id].mx, nb.labels, P.adj_beta[nd.b],
+                                 P.mx + P.fwd[nd.a].mx, alab(id), P.adj_beta[id], P.adj[id].per,
+                                 cbar, P.mx + P.adj[id].mx, alab(nd.b), P.adj_beta[nd.b],
                                  P.adj[nd.b].per, aptr(nd.b), P.mx + P.adj[nd.b].mx, nullptr,
                                  nbeta, nullptr, st.ad, true) ||
-                     make_absorb(net.card, nd.labels, P.adj_beta[id], P.adj[id].per, cbar,
+                     make_absorb(net.card, alab(id), P.adj_beta[id], P.adj[id].per, cbar,
                                  P.mx + P.adj[id].mx, na.labels, na.beta, P.fwd[nd.a].per,
-                                 bfptr(nd.a), P.mx + P.fwd[nd.a].mx, nb.labels, P.adj_beta[nd.b],
+                                 bfptr(nd.a), P.mx + P.fwd[nd.a].mx, alab(nd.b), P.adj_beta[nd.b],
                                  P.adj[nd.b].per, aptr(nd.b), P.mx + P.adj[nd.b].mx, nullptr,
                                  nbeta, nullptr, st.ad, true))) {
                     st.kind = 2;
                 } else if (make_reduce(net.card, na.labels, na.beta, P.fwd[nd.a].per, bfptr(nd.a),
-                                P.mx + P.fwd[nd.a].mx, nd.labels, P.adj_beta[id], P.adj[id].per,
-                                cbar, P.mx + P.adj[id].mx, nb.labels, P.adj_beta[nd.b],
+                                P.mx + P.fwd[nd.a].mx, alab(id), P.adj_beta[id], P.adj[id].per,
+                                cbar, P.mx + P.adj[id].mx, alab(nd.b), P.adj_beta[nd.b],
                                 P.adj[nd.b].per, aptr(nd.b), P.mx + P.adj[nd.b].mx, nbeta, st.rd) &&
                     st.rd.nm >= 4096) {
                     st.kind = 3;
                     scratch = std::max(scratch, reduce_scratch_bytes(st.rd, P.esz));
                 } else if (make_bgemm(net.card, na.labels, na.beta, P.fwd[nd.a].per, bfptr(nd.a),
-                                      P.mx + P.fwd[nd.a].mx, nd.labels, P.adj_beta[id],
-                                      P.adj[id].per, cbar, P.mx + P.adj[id].mx, nb.labels,
+                                      P.mx + P.fwd[nd.a].mx, alab(id), P.adj_beta[id],
+                                      P.adj[id].per, cbar, P.mx + P.adj[id].mx, alab(nd.b),
                                       P.adj_beta[nd.b], P.adj[nd.b].per, aptr(nd.b),
                                       P.mx + P.adj[nd.b].mx, nbeta, P.esz, st.bd, st.btab)) {
                     st.kind = 4;
                     scratch = std::max(scratch, bgemm_scratch_bytes(st.bd, P.esz));
                 } else {
                     err = make_desc(net.card, na.labels, na.beta, P.fwd[nd.a].per, bfptr(nd.a),
-                                    P.mx + P.fwd[nd.a].mx, nd.labels, P.adj_beta[id], P.adj[id].per,
-                                    cbar, P.mx + P.adj[id].mx, nb.labels, P.adj_beta[nd.b],
+                                    P.mx + P.fwd[nd.a].mx, alab(id), P.adj_beta[id], P.adj[id].per,
+                                    cbar, P.mx + P.adj[id].mx, alab(nd.b), P.adj_beta[nd.b],
                                     aptr(nd.b), P.mx + P.adj[nd.b].mx, nullptr, nbeta, nullptr,
                                     st.d);
                     if (!err.empty()) return fail(TN_E_UNSUPPORTED, err);
@@ -1827,9 +1846,9 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
             CDesc d;
             MicroDesc md;
             if (P.need_adj[nd.a]) {
-                err = make_desc(net.card, nd.labels, P.adj_beta[id], P.adj[id].per, cbar,
+                err = make_desc(net.card, alab(id), P.adj_beta[id], P.adj[id].per, cbar,
                                 P.mx + P.adj[id].mx, nb.labels, nb.beta, P.fwd[nd.b].per,
-                                fptr(nd.b), P.mx + P.fwd[nd.b].mx, na.labels, P.adj_beta[nd.a],
+                                fptr(nd.b), P.mx + P.fwd[nd.b].mx, alab(nd.a), P.adj_beta[nd.a],
                                 aptr(nd.a), P.mx + P.adj[nd.a].mx, nullptr, nbeta, nullptr, d);
                 if (!err.empty() || !to_micro(d, P.arena, P.esz, P.mx, P.am, md))
                     return fail(TN_E_UNSUPPORTED, "micro adjoint conversion");
@@ -1837,8 +1856,8 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
             }
             if (P.need_adj[nd.b]) {
                 err = make_desc(net.card, na.labels, na.beta, P.fwd[nd.a].per, fptr(nd.a),
-                                P.mx + P.fwd[nd.a].mx, nd.labels, P.adj_beta[id], P.adj[id].per,
-                                cbar, P.mx + P.adj[id].mx, nb.labels, P.adj_beta[nd.b],
+                                P.mx + P.fwd[nd.a].mx, alab(id), P.adj_beta[id], P.adj[id].per,
+                                cbar, P.mx + P.adj[id].mx, alab(nd.b), P.adj_beta[nd.b],
                                 aptr(nd.b), P.mx + P.adj[nd.b].mx, nullptr, nbeta, nullptr, d);
                 if (!err.empty() || !to_micro(d, P.arena, P.esz, P.mx, P.am, md))
                     return fail(TN_E_UNSUPPORTED, "micro adjoint conversion");
