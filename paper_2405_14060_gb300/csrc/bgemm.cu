@@ -61,8 +61,10 @@ __global__ void __launch_bounds__(kThreads, 2)
     k_bgemm(const __grid_constant__ BDesc d, T *part, int ntiles) {
     constexpr int MT = BM / TM, NT = BN / TN;
     static_assert(MT * NT == kThreads, "thread grid");
-    constexpr int LA = BM * kBK / kThreads, LB = BN * kBK / kThreads;
-    static_assert(LA >= 1 && LB >= 1, "tile loads");
+    // loads per thread and stage (B tiles narrower than the thread count:
+    // the threads past the tile copy nothing)
+    constexpr int LA = BM * kBK / kThreads, LB = (BN * kBK + kThreads - 1) / kThreads;
+    static_assert(LA >= 1 && LA * kThreads == BM * kBK, "tile loads");
     constexpr int RA = BM + 1, RB = BN + 1;              // padded shared rows
     constexpr int SA = kBK * RA, SB = kBK * RB;          // per stage
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -74,6 +76,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     // fixed element mapping of this thread's tile loads: summed index within
     // the stage and shared-memory slot (bytes from the stage's base)
     int ak[LA], bk[LB], am[LA], bn[LB];
+    bool bv[LB];
     uint32_t sdA[LA], sdB[LB];
 #pragma unroll
     for (int r = 0; r < LA; ++r) {
@@ -85,8 +88,9 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
     for (int r = 0; r < LB; ++r) {
         const int e = tid + kThreads * r;
-        bn[r] = d.b_kfast ? e / kBK : e % BN;
-        bk[r] = d.b_kfast ? e % kBK : e / BN;
+        bv[r] = e < BN * kBK;
+        bn[r] = bv[r] ? (d.b_kfast ? e / kBK : e % BN) : 0;
+        bk[r] = bv[r] ? (d.b_kfast ? e % kBK : e / BN) : 0;
         sdB[r] = (uint32_t)((bk[r] * RB + bn[r]) * sizeof(T));
     }
     const uint32_t sA0 = (uint32_t)__cvta_generic_to_shared(As);
@@ -127,6 +131,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             }
 #pragma unroll
             for (int r = 0; r < LB; ++r) {
+                if (!bv[r]) continue;
                 const int k = k0 + bk[r];
                 const bool ok = boff[r] >= 0 && k < p_kend;
                 const T *src = ok ? pB + (boff[r] + __ldg(d.tbk + k)) : pB;
@@ -247,18 +252,20 @@ __global__ void __launch_bounds__(kThreads) k_bgemm_fin(const __grid_constant__ 
 }
 
 // Tile shapes (BM x BN, thread tiles TM x TN): 0 for n > 48, 1 for
-// 16 < n <= 48, 2 for n <= 16.
+// 16 < n <= 48, 2 for 8 < n <= 16, 3 for n <= 8 (128 x 8: the 256 x 16 tile
+// would leave half of every row and, for short rows, half of every column
+// idle).
 template <typename T>
 struct Tiles;
 template <>
 struct Tiles<float> {
-    static constexpr int BM[3] = {128, 256, 256}, BN[3] = {64, 32, 16};
-    static constexpr int TM[3] = {8, 8, 8}, TN[3] = {4, 4, 2};
+    static constexpr int BM[4] = {128, 256, 256, 128}, BN[4] = {64, 32, 16, 8};
+    static constexpr int TM[4] = {8, 8, 8, 4}, TN[4] = {4, 4, 2, 1};
 };
 template <>
 struct Tiles<double> {
-    static constexpr int BM[3] = {64, 64, 128}, BN[3] = {64, 32, 16};
-    static constexpr int TM[3] = {4, 2, 4}, TN[3] = {4, 4, 2};
+    static constexpr int BM[4] = {64, 64, 128, 128}, BN[4] = {64, 32, 16, 8};
+    static constexpr int TM[4] = {4, 2, 4, 4}, TN[4] = {4, 4, 2, 1};
 };
 
 template <typename T>
@@ -306,16 +313,18 @@ void go(const BDesc &d, T *part, int64_t ntiles, cudaStream_t st) {
 // Tile shape and K split; d.tile = -1 when the contraction does not fit the
 // kernels' 31-bit tile and group indices.
 void bgemm_configure(BDesc &d, int elem_bytes) {
-    d.tile = d.N > 48 ? 0 : d.N > 16 ? 1 : 2;
+    d.tile = d.N > 48 ? 0 : d.N > 16 ? 1 : d.N > 8 ? 2 : 3;
     const int bm = elem_bytes == 8 ? Tiles<double>::BM[d.tile] : Tiles<float>::BM[d.tile];
     const int bn = elem_bytes == 8 ? Tiles<double>::BN[d.tile] : Tiles<float>::BN[d.tile];
     const int64_t tiles = ((d.M + bm - 1) / bm) * ((d.N + bn - 1) / bn) * d.G * d.nbeta;
     // split the summed space when the output tiles alone leave most SMs idle
     // and every split still runs several K steps; partials stay under 1 GiB
     int64_t ns = 1;
+    // (then about four waves of two resident blocks per SM, so that the last
+    // wave's idle SMs weigh little)
     const int64_t want = 152LL * 3;
     if (tiles < want && d.K >= 8 * kBK) {
-        ns = std::min<int64_t>((want + tiles - 1) / tiles, d.K / (4 * kBK));
+        ns = std::min<int64_t>((152LL * 8 + tiles - 1) / tiles, d.K / (4 * kBK));
         const int64_t outs = d.G * d.M * d.N * d.nbeta;
         while (ns > 1 && (double)ns * outs * elem_bytes > (double)(1LL << 30)) ns /= 2;
         ns = std::max<int64_t>(1, ns);
@@ -362,7 +371,9 @@ void launch_bgemm(const BDesc &d, void *scratch, cudaStream_t st) {
         case 2: go<T, 1, false>(d, part, ntiles, st); break;
         case 3: go<T, 1, true>(d, part, ntiles, st); break;
         case 4: go<T, 2, false>(d, part, ntiles, st); break;
-        default: go<T, 2, true>(d, part, ntiles, st); break;
+        case 5: go<T, 2, true>(d, part, ntiles, st); break;
+        case 6: go<T, 3, false>(d, part, ntiles, st); break;
+        default: go<T, 3, true>(d, part, ntiles, st); break;
     }
     if (d.nsplit > 1)
         k_bgemm_fin<T><<<(unsigned)((outs + kThreads - 1) / kThreads), kThreads, 0, st>>>(d, part);

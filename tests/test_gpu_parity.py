@@ -327,6 +327,10 @@ CASES = [
     ([2] * 14 + [3], [14] + list(range(13)), list(range(14)), [14, 13]),
     # column side larger than the row side (operand roles swapped)
     ([4, 100, 30], [0, 1], [1, 2], [0, 2]),
+    # at most 8 columns (the 128 x 8 tile): ragged rows, long summed space split
+    ([130, 600, 7], [0, 1], [1, 2], [0, 2]),
+    # 6 columns, a group label fastest in C, summed space split
+    ([3, 9, 2000, 6], [0, 1, 2], [0, 2, 3], [3, 1, 0]),
 ]
 
 
