@@ -10,9 +10,11 @@
 //   k_tc_gemm    tcgen05 tensor-core GEMM: D = X Y^T per batch, X and Y
 //                K-major, TF32 (kind::tf32) or BF16 (kind::f16) inputs staged
 //                by TMA (128-byte swizzle) through a 4-stage mbarrier
-//                pipeline, FP32 accumulator in TMEM (128 x 256 per CTA),
-//                epilogue through tcgen05.ld.  One thread issues TMA, one
-//                issues MMAs, four warps drain TMEM.
+//                pipeline, FP32 accumulators in TMEM (two 128 x 256 buffers
+//                per CTA), epilogue through tcgen05.ld.  One thread issues
+//                TMA, one issues MMAs, four warps drain TMEM; persistent over
+//                tiles for short K, so that a tile's epilogue overlaps the
+//                next tile's MMAs.
 //   k_simt_gemm  CUDA-core tiled GEMM for FP32 and FP64.
 //
 // Every mbarrier wait is bounded in time: a wait that exceeds ~2 s sets the
@@ -481,10 +483,12 @@ void launch_permute(const PDesc &p, cudaStream_t st) {
 constexpr int TC_BM = 128, TC_BN = 256, TC_STAGES = 4;
 constexpr int TC_XBYTES = TC_BM * 128, TC_YBYTES = TC_BN * 128;    // one 128-byte K slab
 constexpr int TC_SMEM = TC_STAGES * (TC_XBYTES + TC_YBYTES) + 1024 + 256;
+constexpr int TC_THREADS = 192;   // warps 0-3 epilogue, warp 4 MMA issuer, warp 5 TMA producer
 
 struct TCParams {
     int64_t R, C, ldd, bsd;
-    int64_t ntn, ntm;           // column / row tiles (grid.x = batch x rows x columns)
+    int64_t ntn, ntm;           // column / row tiles; tiles = batch x rows x columns
+    int64_t ntiles;
     const unsigned long long *mxsx;   // scale of X applied to D (NULL: none)
     int kt;                     // number of 128-byte K slabs
     float *D;
@@ -494,38 +498,61 @@ struct TCParams {
     unsigned long long wait_ns;   // limit of the producer's and the MMA issuer's waits
 };
 
+// Tile t (columns fastest): batch item, first row, first column.
+__device__ __forceinline__ void tc_tile(const TCParams &p, int64_t t, int &bz, int64_t &m0,
+                                        int64_t &n0) {
+    const int64_t per_b = p.ntn * p.ntm;
+    bz = (int)(t / per_b);
+    const int64_t rem = t - (int64_t)bz * per_b;
+    n0 = (rem % p.ntn) * TC_BN;
+    m0 = (rem / p.ntn) * TC_BM;
+}
+
+// Persistent: CTA b takes tiles b, b + grid, ...  The TMA warp fills a ring
+// of TC_STAGES K slabs (X and Y tiles, 128-byte swizzle) across tile
+// boundaries; the MMA warp accumulates tile i into one of two 256-column TMEM
+// buffers (i & 1) while the four epilogue warps drain the other one, so a
+// tile's TMEM -> global epilogue overlaps the next tile's MMAs.  Every wait
+// is bounded: on a timeout the error flag is set, the producer waits for the
+// copies it issued, the MMA warp for the MMAs it issued, and TMEM is freed.
 template <int BF16>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(TC_THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tx, const __grid_constant__ CUtensorMap ty,
               const __grid_constant__ TCParams p) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *sX = smem;
     uint8_t *sY = smem + TC_STAGES * TC_XBYTES;
+    // barriers: full[S], empty[S], tfull[2], tempty[2], fin; then the TMEM slot
     uint64_t *bars = (uint64_t *)(sY + TC_STAGES * TC_YBYTES);
-    uint32_t *tslot = (uint32_t *)(bars + 2 * TC_STAGES + 1);
+    uint32_t *tslot = (uint32_t *)(bars + 2 * TC_STAGES + 5);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // one flat tile index (columns fastest) keeps every grid extent in range
-    const int64_t tl = blockIdx.x, per_b = p.ntn * p.ntm;
-    const int bz = (int)(tl / per_b);
-    const int64_t rem = tl - (int64_t)bz * per_b;
-    const int64_t n0 = (rem % p.ntn) * TC_BN, m0 = (rem / p.ntn) * TC_BM;
     const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + TC_STAGES),
-                   tfull = smem_u32(bars + 2 * TC_STAGES);
+                   tfull0 = smem_u32(bars + 2 * TC_STAGES),
+                   tempty0 = smem_u32(bars + 2 * TC_STAGES + 2),
+                   fin = smem_u32(bars + 2 * TC_STAGES + 4);
+    const int mine = p.ntiles > (int64_t)blockIdx.x
+                         ? (int)((p.ntiles - 1 - (int64_t)blockIdx.x) / gridDim.x) + 1
+                         : 0;
     if (threadIdx.x == 0) {
         for (int s = 0; s < TC_STAGES; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0 + 8 * s));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty0 + 8 * s));
         }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tfull));
+        for (int a = 0; a < 2; ++a) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tfull0 + 8 * a));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(tempty0 + 8 * a),
+                         "r"(TC_BM));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(fin));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(&tx) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(&ty) : "memory");
     }
-    if (warp == 2) {
+    if (warp == 4) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(tslot)),
-                     "r"(TC_BN));
+                     "r"(2 * TC_BN));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_fence_before();
@@ -533,135 +560,180 @@ __global__ void __launch_bounds__(128, 1)
     tc_fence_after();
     const uint32_t tmem = *tslot;
     const int KT = p.kt;
-    if (warp == 0 && lane == 0) {
-        // TMA producer
-        int issued = 0;
-        for (int kt = 0; kt < KT; ++kt) {
-            int s = kt % TC_STAGES, round = kt / TC_STAGES;
-            if (kt >= TC_STAGES && !mbar_wait(empty0 + 8 * s, (round - 1) & 1, p.err, p.wait_ns))
-                break;
-            issued = kt + 1;
-            uint32_t fb = full0 + 8 * s;
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
-                         "r"(TC_XBYTES + TC_YBYTES)
-                         : "memory");
-            int kx = kt * (BF16 ? 64 : 32);
-            asm volatile(
-                "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-                " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(sX + s * TC_XBYTES)),
-                "l"(&tx), "r"(fb), "r"(kx), "r"((int)m0), "r"(bz)
-                : "memory");
-            asm volatile(
-                "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-                " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(sY + s * TC_YBYTES)),
-                "l"(&ty), "r"(fb), "r"(kx), "r"((int)n0), "r"(bz)
-                : "memory");
-        }
-        // the transfers of the last stages issued land before the CTA exits
-        // (already the case when the MMA issuer consumed them; it may have
-        // given up first)
-        for (int kt = issued > TC_STAGES ? issued - TC_STAGES : 0; kt < issued; ++kt)
-            mbar_drain(full0 + 8 * (kt % TC_STAGES), (kt / TC_STAGES) & 1, p.err);
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer: D[128 x 256] (+)= X[128 x K] * Y[256 x K]^T, 4 MMAs of 32 bytes of K per slab
-        const uint32_t idesc = (1u << 4) |                               // D: F32
-                               ((BF16 ? 1u : 2u) << 7) |                 // A: BF16 / TF32
-                               ((BF16 ? 1u : 2u) << 10) |                // B: BF16 / TF32
-                               ((uint32_t)(TC_BN >> 3) << 17) |          // N
-                               ((uint32_t)(TC_BM >> 4) << 24);           // M
-        bool ok = true;
-        for (int kt = 0; kt < KT; ++kt) {
-            int s = kt % TC_STAGES, round = kt / TC_STAGES;
-            if (!mbar_wait(full0 + 8 * s, round & 1, p.err, p.wait_ns)) { ok = false; break; }
-            tc_fence_after();
-            uint64_t ad = sdesc_sw128(smem_u32(sX + s * TC_XBYTES));
-            uint64_t bd = sdesc_sw128(smem_u32(sY + s * TC_YBYTES));
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                uint32_t acc = (kt | kk) ? 1u : 0u;
-                if (BF16)
-                    asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                        "l"(ad + 2 * kk), "l"(bd + 2 * kk), "r"(idesc), "r"(acc));
-                else
-                    asm volatile(
-                        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                        "l"(ad + 2 * kk), "l"(bd + 2 * kk), "r"(idesc), "r"(acc));
-            }
-            asm volatile(
-                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                    empty0 + 8 * s)
-                : "memory");
-        }
-        // arrives once every MMA issued above has completed (also after a
-        // give-up, so that TMEM is released only when idle)
-        (void)ok;
-        asm volatile(
-            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                tfull)
-            : "memory");
-    }
-    __syncwarp();
-    // epilogue: warp w drains TMEM lanes 32w..32w+31 (rows of the tile)
-    bool have = mbar_drain(tfull, 0, p.err) && !*(volatile int *)p.err;
-    have = __all_sync(0xffffffffu, have);
-    tc_fence_after();
-    const int64_t row = m0 + warp * 32 + lane;
-    float mx = 0;
-    const float sxs = p.mxsx ? pow2neg<float>(exp_of_bits(*p.mxsx)) : 1.f;
-    if (have) {
-        float *drow = p.D + (int64_t)bz * p.bsd + row * p.ldd;
-        for (int ch = 0; ch < TC_BN / 32; ++ch) {
-            if (n0 + ch * 32 >= p.C) break;   // warp-uniform: no columns left
-            uint32_t r[32];
-            uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 32);
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
-                "%10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, "
-                "%26, %27, %28, %29, %30, %31}, [%32];"
-                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                  "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-                  "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
-                  "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-                  "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
-                  "=r"(r[30]), "=r"(r[31])
-                : "r"(ta));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            int64_t c0 = n0 + ch * 32;
-            if (row < p.R && c0 < p.C) {
-                if (c0 + 32 <= p.C && (p.ldd % 4) == 0) {
-                    float4 *dst = (float4 *)(drow + c0);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        float4 v;
-                        v.x = __uint_as_float(r[4 * q + 0]) * sxs;
-                        v.y = __uint_as_float(r[4 * q + 1]) * sxs;
-                        v.z = __uint_as_float(r[4 * q + 2]) * sxs;
-                        v.w = __uint_as_float(r[4 * q + 3]) * sxs;
-                        dst[q] = v;
-                        mx = fmaxf(mx, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
+    if (warp == 5) {
+        if (lane == 0) {
+            // ------------------------------------------------ TMA producer
+            int q = 0;   // K slabs issued so far (all tiles)
+            bool ok = true;
+            for (int li = 0; li < mine && ok; ++li) {
+                int bz;
+                int64_t m0, n0;
+                tc_tile(p, (int64_t)blockIdx.x + (int64_t)li * gridDim.x, bz, m0, n0);
+                for (int kt = 0; kt < KT; ++kt, ++q) {
+                    const int s = q % TC_STAGES;
+                    if (q >= TC_STAGES &&
+                        !mbar_wait(empty0 + 8 * s, ((q / TC_STAGES) - 1) & 1, p.err, p.wait_ns)) {
+                        ok = false;
+                        break;
                     }
-                } else {
-                    for (int q = 0; q < 32 && c0 + q < p.C; ++q) {
-                        float v = __uint_as_float(r[q]) * sxs;
-                        drow[c0 + q] = v;
-                        mx = fmaxf(mx, v);
+                    const uint32_t fb = full0 + 8 * s;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb),
+                                 "r"(TC_XBYTES + TC_YBYTES)
+                                 : "memory");
+                    const int kx = kt * (BF16 ? 64 : 32);
+                    asm volatile(
+                        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(sX + s * TC_XBYTES)),
+                        "l"(&tx), "r"(fb), "r"(kx), "r"((int)m0), "r"(bz)
+                        : "memory");
+                    asm volatile(
+                        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+                        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(sY + s * TC_YBYTES)),
+                        "l"(&ty), "r"(fb), "r"(kx), "r"((int)n0), "r"(bz)
+                        : "memory");
+                }
+            }
+            // the last transfers issued land before the CTA exits (already
+            // the case when the MMA warp consumed them; it may have given up)
+            for (int r = q > TC_STAGES ? q - TC_STAGES : 0; r < q; ++r)
+                mbar_drain(full0 + 8 * (r % TC_STAGES), (r / TC_STAGES) & 1, p.err);
+        }
+        __syncwarp();
+    } else if (warp == 4) {
+        if (lane == 0) {
+            // ------------------------------------------------- MMA issuer
+            // D[128 x 256] (+)= X[128 x K] * Y[256 x K]^T, 4 MMAs of 32 bytes of K per slab
+            const uint32_t idesc = (1u << 4) |                               // D: F32
+                                   ((BF16 ? 1u : 2u) << 7) |                 // A: BF16 / TF32
+                                   ((BF16 ? 1u : 2u) << 10) |                // B: BF16 / TF32
+                                   ((uint32_t)(TC_BN >> 3) << 17) |          // N
+                                   ((uint32_t)(TC_BM >> 4) << 24);           // M
+            int q = 0;
+            bool ok = true;
+            for (int li = 0; li < mine && ok; ++li) {
+                const int a = li & 1;
+                // the epilogue has drained this TMEM buffer (tile li - 2)
+                if (li >= 2 && !mbar_wait(tempty0 + 8 * a, ((li >> 1) - 1) & 1, p.err, p.wait_ns)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t acc_t = tmem + (uint32_t)(a * TC_BN);
+                for (int kt = 0; kt < KT; ++kt, ++q) {
+                    const int s = q % TC_STAGES;
+                    if (!mbar_wait(full0 + 8 * s, (q / TC_STAGES) & 1, p.err, p.wait_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t ad = sdesc_sw128(smem_u32(sX + s * TC_XBYTES));
+                    const uint64_t bd = sdesc_sw128(smem_u32(sY + s * TC_YBYTES));
+#pragma unroll
+                    for (int kk = 0; kk < 4; ++kk) {
+                        const uint32_t accum = (kt | kk) ? 1u : 0u;
+                        if (BF16)
+                            asm volatile(
+                                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                                    acc_t),
+                                "l"(ad + 2 * kk), "l"(bd + 2 * kk), "r"(idesc), "r"(accum));
+                        else
+                            asm volatile(
+                                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                                    acc_t),
+                                "l"(ad + 2 * kk), "l"(bd + 2 * kk), "r"(idesc), "r"(accum));
+                    }
+                    asm volatile(
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                            empty0 + 8 * s)
+                        : "memory");
+                }
+                if (ok)
+                    asm volatile(
+                        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                            tfull0 + 8 * a)
+                        : "memory");
+            }
+            // completes once every MMA issued above has finished (also after
+            // a give-up), so that TMEM is idle when it is released
+            (void)ok;
+            asm volatile(
+                "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(fin)
+                : "memory");
+            mbar_drain(fin, 0, p.err);
+        }
+        __syncwarp();
+    } else {
+        // ----------------------------------------------------- epilogue
+        // warp w drains TMEM lanes 32w..32w+31 (rows of the tile)
+        const float sxs = p.mxsx ? pow2neg<float>(exp_of_bits(*p.mxsx)) : 1.f;
+        for (int li = 0; li < mine; ++li) {
+            const int a = li & 1;
+            bool have = mbar_wait(tfull0 + 8 * a, (li >> 1) & 1, p.err, p.wait_ns);
+            have = __all_sync(0xffffffffu, have);
+            if (!have) break;
+            tc_fence_after();
+            int bz;
+            int64_t m0, n0;
+            tc_tile(p, (int64_t)blockIdx.x + (int64_t)li * gridDim.x, bz, m0, n0);
+            const int64_t row = m0 + warp * 32 + lane;
+            float mx = 0;
+            float *drow = p.D + (int64_t)bz * p.bsd + row * p.ldd;
+            for (int ch = 0; ch < TC_BN / 32; ++ch) {
+                if (n0 + ch * 32 >= p.C) break;   // warp-uniform: no columns left
+                uint32_t r[32];
+                const uint32_t ta =
+                    tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * TC_BN + ch * 32);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+                    "%10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, "
+                    "%26, %27, %28, %29, %30, %31}, [%32];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                      "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                      "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
+                      "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+                      "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+                      "=r"(r[30]), "=r"(r[31])
+                    : "r"(ta));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                const int64_t c0 = n0 + ch * 32;
+                if (row < p.R) {
+                    if (c0 + 32 <= p.C && (p.ldd % 4) == 0) {
+                        float4 *dst = (float4 *)(drow + c0);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            float4 v;
+                            v.x = __uint_as_float(r[4 * j + 0]) * sxs;
+                            v.y = __uint_as_float(r[4 * j + 1]) * sxs;
+                            v.z = __uint_as_float(r[4 * j + 2]) * sxs;
+                            v.w = __uint_as_float(r[4 * j + 3]) * sxs;
+                            dst[j] = v;
+                            mx = fmaxf(mx, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
+                        }
+                    } else {
+                        for (int j = 0; j < 32 && c0 + j < p.C; ++j) {
+                            const float v = __uint_as_float(r[j]) * sxs;
+                            drow[c0 + j] = v;
+                            mx = fmaxf(mx, v);
+                        }
                     }
                 }
             }
+            // this TMEM buffer may take the MMAs of tile li + 2
+            tc_fence_before();
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tempty0 + 8 * a) : "memory");
+            const int64_t beta = p.beta_div_batch > 0 ? (int64_t)bz / p.beta_div_batch
+                                 : p.beta_div_row > 0 ? (row < p.R ? row : p.R - 1) / p.beta_div_row
+                                                      : 0;
+            record_max(p.mxd, beta, row < p.R, (double)mx);
         }
     }
-    int64_t beta = p.beta_div_batch > 0 ? (int64_t)bz / p.beta_div_batch
-                   : p.beta_div_row > 0 ? (row < p.R ? row : p.R - 1) / p.beta_div_row
-                                        : 0;
-    record_max(p.mxd, beta, have && row < p.R, (double)mx);
     tc_fence_before();
     __syncthreads();
-    if (warp == 2)
+    if (warp == 4)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(TC_BN));
+                     "r"(2 * TC_BN));
 }
 
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -734,10 +806,25 @@ cudaError_t launch_tc_gemm(const GDesc &g, int *err_flag, cudaStream_t st) {
     if (const char *w = getenv("TN_TEST_TC_WAIT_NS")) p.wait_ns = strtoull(w, nullptr, 10);
     p.ntn = (g.C + TC_BN - 1) / TC_BN;
     p.ntm = (g.R + TC_BM - 1) / TC_BM;
-    if (p.ntn * p.ntm * g.batch >= (1LL << 31)) return cudaErrorInvalidConfiguration;
-    dim3 grid((unsigned)(p.ntn * p.ntm * g.batch), 1, 1);
-    if (bf16) k_tc_gemm<1><<<grid, 128, TC_SMEM, st>>>(mx, my, p);
-    else k_tc_gemm<0><<<grid, 128, TC_SMEM, st>>>(mx, my, p);
+    p.ntiles = p.ntn * p.ntm * g.batch;
+    if (p.ntiles >= (1LL << 31)) return cudaErrorInvalidConfiguration;
+    // short K (at most 64 slabs): persistent, one CTA per SM (its shared
+    // memory and the whole TMEM), each tile's epilogue overlapping the next
+    // tile's MMAs; long K: one tile per CTA (the epilogue is a small part of
+    // the tile, and CTAs started in tile order keep the concurrently read
+    // operand panels close together in L2, where persistent CTAs drift apart
+    // over hundreds of K slabs; measured on the batched workload's nodes)
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0, n = 0;
+        nsm = (cudaGetDevice(&dev) == cudaSuccess &&
+               cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n > 0)
+                  ? n
+                  : 152;
+    }
+    dim3 grid((unsigned)(p.kt <= 64 ? std::min<int64_t>(p.ntiles, nsm) : p.ntiles), 1, 1);
+    if (bf16) k_tc_gemm<1><<<grid, TC_THREADS, TC_SMEM, st>>>(mx, my, p);
+    else k_tc_gemm<0><<<grid, TC_THREADS, TC_SMEM, st>>>(mx, my, p);
     return cudaGetLastError();
 }
 

@@ -331,6 +331,10 @@ CASES = [
     ([130, 600, 7], [0, 1], [1, 2], [0, 2]),
     # 6 columns, a group label fastest in C, summed space split
     ([3, 9, 2000, 6], [0, 1, 2], [0, 2, 3], [3, 1, 0]),
+    # at least 128 columns: ragged both ways
+    ([200, 45, 300], [0, 1], [1, 2], [0, 2]),
+    # the same with a group label and the rows fastest in C
+    ([2, 150, 20, 130], [0, 1, 2], [0, 2, 3], [0, 3, 1]),
 ]
 
 
