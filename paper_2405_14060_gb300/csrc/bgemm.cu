@@ -43,13 +43,19 @@ struct TilePos {
 __device__ __forceinline__ TilePos tile_pos(const BDesc &d, int64_t t, int BM, int BN) {
     const int64_t tiles_m = (d.M + BM - 1) / BM, tiles_n = (d.N + BN - 1) / BN;
     TilePos p;
-    int64_t r;
-    int64_t q = div_tile(t, tiles_m, log2_if_pow2(tiles_m), r);
+    int64_t r, q = t;
+    if (d.c_gfast) {
+        q = div_tile(q, d.G, log2_if_pow2(d.G), r);
+        p.g = r;
+    }
+    q = div_tile(q, tiles_m, log2_if_pow2(tiles_m), r);
     p.m0 = r * BM;
     q = div_tile(q, tiles_n, log2_if_pow2(tiles_n), r);
     p.n0 = r * BN;
-    q = div_tile(q, d.G, log2_if_pow2(d.G), r);
-    p.g = r;
+    if (!d.c_gfast) {
+        q = div_tile(q, d.G, log2_if_pow2(d.G), r);
+        p.g = r;
+    }
     q = div_tile(q, d.nbeta, log2_if_pow2(d.nbeta), r);
     p.beta = r;
     p.split = (int)q;

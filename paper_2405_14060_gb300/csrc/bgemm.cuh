@@ -26,6 +26,11 @@ struct BDesc {
     int a_kfast;                   // A's fastest label is summed (else it is in M or G)
     int b_kfast;                   // B's fastest label is summed (else in N or G)
     int c_nfast;                   // C's fastest label is in N (else in M or G)
+    int c_gfast;                   // a G label lies inside C's 32-byte sectors: tiles
+                                   // enumerate G fastest, so that the tiles writing
+                                   // the same sectors run together (their partial
+                                   // writes merge in L2 instead of each eviction
+                                   // costing a DRAM read-modify-write)
     const void *A, *B;
     void *C;
     const unsigned long long *mxa, *mxb;

@@ -991,6 +991,11 @@ static bool make_bgemm(const std::vector<int> &card, const Labels &lx, bool bx, 
     d.a_kfast = in(K, fastest(lx)) ? 1 : 0;
     d.b_kfast = in(K, fastest(ly)) ? 1 : 0;
     d.c_nfast = in(N, fastest(lo)) ? 1 : 0;
+    // a group label inside C's 32-byte sectors: tiles enumerate G fastest,
+    // so the tiles sharing a sector write it at about the same time
+    d.c_gfast = 0;
+    for (int v : G)
+        if (card[v] > 1 && stride_in(card, lo, v) * esz < 32) d.c_gfast = 1;
     d.nbeta = bo ? nbeta : 1;
     d.bsa = (bo && bx) ? perx : 0;
     d.bsb = (bo && by) ? pery : 0;
@@ -1965,6 +1970,22 @@ tn_status build_program(tn_model *m, const Net &net, const Tree &tree, int kind,
                     for (const int32_t **q : {&b.tag, &b.tbg, &b.tcg, &b.tam, &b.tcm, &b.tbn,
                                               &b.tcn, &b.tak, &b.tbk})
                         *q = base + (intptr_t)*q;
+                    if (getenv("TN_PLAN_TRACE") && getenv("TN_PLAN_TRACE")[0] == '1') {
+                        // plan trace: the first offsets of each group table
+                        const std::vector<int32_t> &t = w.first->btab;
+                        const int64_t sz[9] = {b.G, b.G, b.G, b.M, b.M, b.N, b.N, b.K, b.K};
+                        const char *nm[9] = {"ag", "bg", "cg", "am", "cm", "bn", "cn", "ak", "bk"};
+                        int64_t at = 0;
+                        fprintf(stderr, "bgemm tables G %lld M %lld N %lld K %lld:",
+                                (long long)b.G, (long long)b.M, (long long)b.N, (long long)b.K);
+                        for (int q = 0; q < 9; ++q) {
+                            fprintf(stderr, " %s", nm[q]);
+                            for (int64_t i = 0; i < std::min<int64_t>(sz[q], 8); ++i)
+                                fprintf(stderr, ",%d", t[at + i]);
+                            at += sz[q];
+                        }
+                        fprintf(stderr, "\n");
+                    }
                     w.first->btab.clear();
                     w.first->btab.shrink_to_fit();
                 }

@@ -498,14 +498,21 @@ struct TCParams {
     unsigned long long wait_ns;   // limit of the producer's and the MMA issuer's waits
 };
 
-// Tile t (columns fastest): batch item, first row, first column.
+// Tile t: batch item, first row, first column.  Within a batch item the
+// row tiles go in groups of TC_GROUP, and a group's tiles run rows fastest,
+// so that the tiles processed together read a few row panels of X and a few
+// column panels of Y (which then stay in L2) rather than all of Y.
+constexpr int TC_GROUP = 8;
 __device__ __forceinline__ void tc_tile(const TCParams &p, int64_t t, int &bz, int64_t &m0,
                                         int64_t &n0) {
     const int64_t per_b = p.ntn * p.ntm;
     bz = (int)(t / per_b);
     const int64_t rem = t - (int64_t)bz * per_b;
-    n0 = (rem % p.ntn) * TC_BN;
-    m0 = (rem / p.ntn) * TC_BM;
+    const int64_t per_g = (int64_t)TC_GROUP * p.ntn;
+    const int64_t grp = rem / per_g, loc = rem - grp * per_g;
+    const int64_t rows = min((int64_t)TC_GROUP, p.ntm - grp * TC_GROUP);
+    m0 = (grp * TC_GROUP + loc % rows) * TC_BM;
+    n0 = (loc / rows) * TC_BN;
 }
 
 // Persistent: CTA b takes tiles b, b + grid, ...  The TMA warp fills a ring

@@ -955,3 +955,23 @@ def test_workload5_sliced_pr_mar_and_sampling():
     assert np.all(np.abs(freq - 0.5) < 5 * np.sqrt(0.25 / n))
     mag = (2 * s.astype(np.int64) - 1).sum(axis=1)
     assert abs(mag.mean()) < 5 * mag.std() / np.sqrt(n)
+
+
+def test_workload5_fp64_two_trees():
+    """Workload 5 has no oracle value (its treewidth is beyond the CPU
+    elimination).  Consistency instead: FP64 log Z on two different trees
+    from the same annealing run (seed 1) -- absorption chains re-associated
+    and sliced to per-slice space 2^30 (4 slice variables), and as found,
+    sliced to 2^28 (7 slice variables) -- agree to 1e-11 relative.  Not an
+    oracle check: both runs use this library's FP64 path."""
+    w = synth.workload(5)
+    M = tn.Model.from_synth(w.model)
+    l0, r0 = M.optimize_order(2, 20, 1)
+    lz, sets = [], []
+    for (l, r), space in ((M.reassociate(l0, r0), 30), ((l0, r0), 28)):
+        sl = M.choose_slices(space, 12, l, r)
+        M.set_order(l, r, slice_vars=sl)
+        sets.append(sorted(sl))
+        lz.append(M.pr(prec="fp64")[0])
+    assert sets[0] != sets[1]
+    assert abs(lz[0] - lz[1]) <= 1e-11 * abs(lz[0]), lz
