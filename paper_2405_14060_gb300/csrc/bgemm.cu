@@ -163,14 +163,14 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
     for (int s = 0; s < kStages - 1; ++s) issue();
     int c_li = 0, c_ks = 0, c_stage = 0;
+    const bool kshort = d.nsplit == 1 && d.K <= kBK / 2;
     while (c_li < mine) {
         cp_async_wait<kStages - 2>();
         __syncthreads();
         issue();
         const T *sa = As + c_stage * SA + im;
         const T *sb = Bs + c_stage * SB + in;
-#pragma unroll
-        for (int kk = 0; kk < kBK; ++kk) {
+        auto kstep = [&](int kk) {
             T a[TM], bv[TN];
 #pragma unroll
             for (int i = 0; i < TM; ++i) a[i] = sa[kk * RA + i * MT];
@@ -180,6 +180,14 @@ __global__ void __launch_bounds__(kThreads, 2)
             for (int i = 0; i < TM; ++i)
 #pragma unroll
                 for (int j = 0; j < TN; ++j) acc[i][j] += a[i] * bv[j];
+        };
+        if (kshort) {
+            // summed space of at most half a stage: the other half is zeros
+#pragma unroll
+            for (int kk = 0; kk < kBK / 2; ++kk) kstep(kk);
+        } else {
+#pragma unroll
+            for (int kk = 0; kk < kBK; ++kk) kstep(kk);
         }
         c_stage = c_stage == kStages - 1 ? 0 : c_stage + 1;
         if (++c_ks < nks) continue;

@@ -335,6 +335,9 @@ CASES = [
     ([200, 45, 300], [0, 1], [1, 2], [0, 2]),
     # the same with a group label and the rows fastest in C
     ([2, 150, 20, 130], [0, 1, 2], [0, 2, 3], [0, 3, 1]),
+    # summed space of at most 8 (half K steps): K = 6, and K = 8 with a group
+    ([150, 6, 90], [0, 1], [1, 2], [0, 2]),
+    ([2, 130, 8, 20], [0, 1, 2], [0, 2, 3], [0, 1, 3]),
 ]
 
 
