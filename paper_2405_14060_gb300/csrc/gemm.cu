@@ -265,8 +265,9 @@ void plan_permute_tiles(PDesc &p, std::vector<int32_t> &tab) {
     int64_t n = 1;
     bool full = false;
     // dims below `lim` on one side (lim < 0: the next input-fastest dims
-    // until the tile holds 2048 entries)
-    auto add_below = [&](bool by_in, int64_t lim) {
+    // until the tile holds 2048 entries), up to `cap` entries in the tile (a
+    // dim that would pass it is split; at PT_MAXN the tile is full)
+    auto add_below = [&](bool by_in, int64_t lim, int64_t cap) {
         while (!full && (lim > 0 || n < 2048)) {
             int best = -1;
             for (int i = 0; i < (int)d.size(); ++i) {
@@ -276,12 +277,12 @@ void plan_permute_tiles(PDesc &p, std::vector<int32_t> &tab) {
                 if (best < 0 || st < (by_in ? d[best].sin : d[best].sout)) best = i;
             }
             if (best < 0) return;
-            if (n * d[best].sz <= PT_MAXN) {
+            if (n * d[best].sz <= cap) {
                 in_u[best] = 1;
                 n *= d[best].sz;
                 continue;
             }
-            int64_t lo = PT_MAXN / n;
+            int64_t lo = cap / n;
             while (lo >= 2 && d[best].sz % lo) --lo;
             if (lo >= 2) {
                 D hi{d[best].sz / lo, d[best].sin * lo, d[best].sout * lo, false};
@@ -291,12 +292,17 @@ void plan_permute_tiles(PDesc &p, std::vector<int32_t> &tab) {
                 in_u.insert(in_u.begin() + best + 1, 1);
                 n *= lo;
             }
-            full = true;
+            if (cap >= PT_MAXN) full = true;
+            return;
         }
     };
-    add_below(true, RUN);
-    add_below(false, RUN);
-    add_below(true, -1);
+    // the input's contiguous side first, but at most 128 entries of it, so
+    // that a long contiguous input run (a plain transpose) still leaves room
+    // for at least 32 contiguous outputs; then the output's; then more of
+    // the input's
+    add_below(true, RUN, 4 * RUN);
+    add_below(false, RUN, PT_MAXN);
+    add_below(true, -1, PT_MAXN);
     if (n < 256) return;
     std::vector<int> U;
     for (int i = 0; i < (int)d.size(); ++i)
