@@ -48,23 +48,25 @@ TREE = (3, 12, 2)            # order search: method 3 (bisection + annealing), r
 GOLDEN = os.path.join(ROOT, "tests", "golden", "fullsize_oracle.json")
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) over the
-# algorithmic bytes of the same launches, from one ncu capture per kernel
-# class on a small case of this workload (2 evidence sets for the operand
-# preparation, the largest batched-GEMM shape for k_bgemm); both kernels'
+# DRAM traffic (ncu dram__bytes.sum.per_second x gpu__time_duration.sum, read
+# plus write) over the algorithmic bytes of the same launches, from one ncu
+# capture per kernel
+# class on a small case of this workload (2 evidence sets); both kernels'
 # traffic grows in proportion to the entries they move, so the ratio carries
 # to the 128-set launches.  Valid only while the sources hash to the values
 # recorded with the capture.
 TRAFFIC = {
-    # DRAM bytes (ncu rate x duration) of the two large k_permute_tiled
+    # DRAM bytes (ncu rate x duration) of the four large k_permute_tiled
     # launches of a 2-set pass over their algorithmic bytes (2^26 FP32 entries
     # read, written as BF16)
-    "prep": {"ratio": (373.1 + 373.4) / (2 * 402.65),
+    "prep": {"ratio": (374.0 + 373.1 + 373.5 + 373.3) / (4 * 402.65),
              "sources": {"paper_2405_14060_gb300/csrc/gemm.cu":
-                         "86a23d96010b1f5fa899162ce17cc0b6c6a43e8c1e850c58cae8dd8afddef8bc"}},
-    "bgemm": {"ratio": (1.141243 + 1.029389) / (2 * 1.073741824),
+                         "19d0d851ea2d057c1502d0358f269e6573decbd76c1eb3aab1fd7a643fee6035"}},
+    # the two large k_bgemm launches of a 2-set pass (the K = 8 node and the
+    # n 1024, k 32 node) over their algorithmic bytes
+    "bgemm": {"ratio": (232.2 + 220.3) / (285.2 + 277.3),
               "sources": {"paper_2405_14060_gb300/csrc/bgemm.cu":
-                          "65ddccb1d707afe939cf663c2e54200c1e2727c7525428acf6687b4a2e8ae4b0"}},
+                          "655f11c3e91fa828a9610a506da98886a5889bd2ce2696ae942b9da987bbacad"}},
 }
 
 
