@@ -9,8 +9,9 @@
 //                    in shared memory as [s][t]; tiles of 128 positions r of X
 //                    staged by asynchronous copies two tiles ahead (as [s][p]
 //                    when positions are contiguous in X, as [p][s] when the
-//                    summed combinations are); each thread owns 4 positions x
-//                    4 new combinations and reads 16-byte vectors of both.
+//                    summed combinations are); each of 128 threads owns 8
+//                    positions x 4 new combinations and reads 16-byte vectors
+//                    of both (three shared loads per 32 multiply-adds).
 //   k_reduce_dense   O[g, s, t] = sum_m X[g, m, s] Z[g, m, t]: tiles of 64
 //                    positions of both operands staged as [p][s | t]; four
 //                    thread groups take a quarter of each tile's positions,
@@ -111,6 +112,7 @@ struct DenseModes {
 };
 
 constexpr int AD_P = 128;   // positions per tile
+constexpr int AD_T = 128;   // threads: 8 positions x 4 new combinations each
 constexpr int AD_S = 3;     // tile buffers
 
 template <typename T>
@@ -167,7 +169,7 @@ __device__ __forceinline__ void scatter4(T *dst, uint2 w, const T (&v)[4]) {
 // combinations per store (all from registers), 3 through shared memory as
 // the tile's chunks in memory order (chunk table at d.cyo).
 template <typename T, int XM>
-__global__ void __launch_bounds__(256, 3) k_absorb_dense(const __grid_constant__ ADesc d, int ym) {
+__global__ void __launch_bounds__(AD_T) k_absorb_dense(const __grid_constant__ ADesc d, int ym) {
     extern __shared__ __align__(16) unsigned char smraw[];
     constexpr int PAD = ad_pad<T>();
     constexpr int WR = 32 + PAD;                       // W row: [s][t]
@@ -186,7 +188,7 @@ __global__ void __launch_bounds__(256, 3) k_absorb_dense(const __grid_constant__
     const int nqx = d.ns * (AD_P / 4), nqy = d.nt * (AD_P / 4);
     {
         const T *Wg = (const T *)d.W + beta * d.bsw;
-        for (int i = tid; i < 32 * 32; i += 256) {
+        for (int i = tid; i < 32 * 32; i += AD_T) {
             const int s = i >> 5, t = i & 31;
             Ws[s * WR + t] = (s < d.ns && t < d.nt) ? __ldg(Wg + d.wso[s] + d.wto[t]) : T(0);
         }
@@ -202,13 +204,14 @@ __global__ void __launch_bounds__(256, 3) k_absorb_dense(const __grid_constant__
     const T *X = (const T *)d.X + beta * d.bsx;
     T *Y = (T *)d.Y + beta * d.bsy;
     const uint32_t xs0 = (uint32_t)__cvta_generic_to_shared(Xs);
-    // X chunk mode: this thread's chunks q = tid + 256 r are the same in
+    // X chunk mode: this thread's chunks q = tid + AD_T r are the same in
     // every tile, so their offsets and slots stay in registers
-    int32_t xrel[4];
-    uint2 xsl[4];
+    constexpr int NQ = 32 * (AD_P / 4) / AD_T;
+    int32_t xrel[NQ];
+    uint2 xsl[NQ];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int q = tid + 256 * r;
+    for (int r = 0; r < NQ; ++r) {
+        const int q = tid + AD_T * r;
         xrel[r] = 0;
         xsl[r] = make_uint2(0u, 0u);
         if (XM == 3 && q < nqx) {
@@ -229,14 +232,14 @@ __global__ void __launch_bounds__(256, 3) k_absorb_dense(const __grid_constant__
             if (XM == 3) {
                 const T *Xt = Xo + __ldg(tx + j0);
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const int q = tid + 256 * r;
+                for (int r = 0; r < NQ; ++r) {
+                    const int q = tid + AD_T * r;
                     if (q < nqx)
                         cp_async4<T>(sb + (uint32_t)(4 * q * sizeof(T)), Xt + xrel[r], true);
                 }
             } else if (XM == 1) {
                 // 32 rows x 32 quads of positions
-                for (int e = tid; e < 32 * (AD_P / 4); e += 256) {
+                for (int e = tid; e < 32 * (AD_P / 4); e += AD_T) {
                     const int s = e / (AD_P / 4), p = (e % (AD_P / 4)) * 4;
                     const int j = j0 + p;
                     const bool ok = s < d.ns && j < nin;
@@ -245,7 +248,7 @@ __global__ void __launch_bounds__(256, 3) k_absorb_dense(const __grid_constant__
                 }
             } else if (XM == 2) {
                 // AD_P rows x 8 quads of summed combinations
-                for (int e = tid; e < AD_P * 8; e += 256) {
+                for (int e = tid; e < AD_P * 8; e += AD_T) {
                     const int p = e >> 3, s = (e & 7) * 4;
                     const int j = j0 + p;
                     const bool ok = s < d.ns && j < nin;
@@ -253,7 +256,7 @@ __global__ void __launch_bounds__(256, 3) k_absorb_dense(const __grid_constant__
                                  ok ? Xo + __ldg(tx + j) + d.xoff[s] : Xo, ok);
                 }
             } else {
-                for (int e = tid; e < 32 * AD_P; e += 256) {
+                for (int e = tid; e < 32 * AD_P; e += AD_T) {
                     const int s = e / AD_P, p = e % AD_P;
                     const int j = j0 + p;
                     const bool ok = s < d.ns && j < nin;
@@ -264,7 +267,7 @@ __global__ void __launch_bounds__(256, 3) k_absorb_dense(const __grid_constant__
         }
         cp_async_commit();
     };
-    const int pg = tid >> 3, tg = tid & 7;   // positions 4 pg + i, new combinations 4 tg + j
+    const int pg = tid >> 3, tg = tid & 7;   // positions 8 pg + i, new combinations 4 tg + j
     T mx = 0;
     issue(0, 0);
     issue(1, 1);
@@ -278,8 +281,8 @@ __global__ void __launch_bounds__(256, 3) k_absorb_dense(const __grid_constant__
         const T *xb = tb;
         if (XM == 3) {
 #pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                const int q = tid + 256 * r;
+            for (int r = 0; r < NQ; ++r) {
+                const int q = tid + AD_T * r;
                 if (q < nqx) {
                     T v[4];
                     ld4(tb + 4 * q, v);
@@ -289,22 +292,22 @@ __global__ void __launch_bounds__(256, 3) k_absorb_dense(const __grid_constant__
             __syncthreads();
             xb = Xc;
         }
-        T acc[4][4];
+        T acc[8][4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 8; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
         if (XM == 2) {
             for (int s = 0; s < ns4; s += 4) {
-                T xv[4][4], wv[4][4];
+                T xv[8][4], wv[4][4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) ld4(xb + (4 * pg + i) * RX + s, xv[i]);
+                for (int i = 0; i < 8; ++i) ld4(xb + (8 * pg + i) * RX + s, xv[i]);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) ld4(Ws + (s + q) * WR + 4 * tg, wv[q]);
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
+                    for (int i = 0; i < 8; ++i)
 #pragma unroll
                         for (int j = 0; j < 4; ++j) acc[i][j] += xv[i][q] * wv[q][j];
             }
@@ -312,11 +315,12 @@ __global__ void __launch_bounds__(256, 3) k_absorb_dense(const __grid_constant__
             // chunk mode fills only the rows s < ns
             const int send = XM == 3 ? d.ns : ns4;
             for (int s = 0; s < send; ++s) {
-                T xv[4], wv[4];
-                ld4(xb + s * RS + 4 * pg, xv);
+                T xv[8], wv[4];
+                ld4(xb + s * RS + 8 * pg, *(T(*)[4])xv);
+                ld4(xb + s * RS + 8 * pg + 4, *(T(*)[4])(xv + 4));
                 ld4(Ws + s * WR + 4 * tg, wv);
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+                for (int i = 0; i < 8; ++i)
 #pragma unroll
                     for (int j = 0; j < 4; ++j) acc[i][j] += xv[i] * wv[j];
             }
@@ -326,7 +330,7 @@ __global__ void __launch_bounds__(256, 3) k_absorb_dense(const __grid_constant__
         int64_t bx = 0, by = 0;
         absorb_outer(d, o, nod, bx, by);
         T *Yo = Y + by;
-        const int j0 = (int)crem * AD_P + 4 * pg;
+        const int j0 = (int)crem * AD_P + 8 * pg;
         const int t0 = 4 * tg;
         if (ym == 3) {
             // [t][p] in shared memory, then the tile's chunks in memory order
@@ -335,36 +339,44 @@ __global__ void __launch_bounds__(256, 3) k_absorb_dense(const __grid_constant__
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 if (t0 + j >= d.nt) break;
-                st4(ys + (t0 + j) * RS + 4 * pg, acc[0][j] * scale, acc[1][j] * scale,
-                    acc[2][j] * scale, acc[3][j] * scale);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) mx = mx > acc[i][j] ? mx : acc[i][j];
+                for (int h = 0; h < 2; ++h)
+                    st4(ys + (t0 + j) * RS + 8 * pg + 4 * h, acc[4 * h][j] * scale,
+                        acc[4 * h + 1][j] * scale, acc[4 * h + 2][j] * scale,
+                        acc[4 * h + 3][j] * scale);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) mx = mx > acc[i][j] ? mx : acc[i][j];
             }
             __syncthreads();
             T *Yt = Yo + __ldg(ty + (int)crem * AD_P);
             const int32_t *cry = d.tab + d.cyo;
             const uint2 *csy = (const uint2 *)(d.tab + d.cyo + nqy);
-            for (int q = tid; q < nqy; q += 256) {
+            for (int q = tid; q < nqy; q += AD_T) {
                 const uint2 w = __ldg(csy + q);
                 st4(Yt + __ldg(cry + q), ys[w.x & 0xffffu], ys[w.x >> 16], ys[w.y & 0xffffu],
                     ys[w.y >> 16]);
             }
         } else if (ym == 1) {
-            if (j0 < nin) {
-                const int oy = __ldg(ty + j0);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int jq = j0 + 4 * h;   // a quad of positions: all valid or none
+                if (jq >= nin) continue;
+                const int oy = __ldg(ty + jq);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     if (t0 + j >= d.nt) break;
-                    st4(Yo + oy + d.yoff[t0 + j], acc[0][j] * scale, acc[1][j] * scale,
-                        acc[2][j] * scale, acc[3][j] * scale);
+                    st4(Yo + oy + d.yoff[t0 + j], acc[4 * h][j] * scale,
+                        acc[4 * h + 1][j] * scale, acc[4 * h + 2][j] * scale,
+                        acc[4 * h + 3][j] * scale);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) mx = mx > acc[i][j] ? mx : acc[i][j];
+                    for (int i = 0; i < 4; ++i)
+                        mx = mx > acc[4 * h + i][j] ? mx : acc[4 * h + i][j];
                 }
             }
         } else if (ym == 2) {
             if (t0 < d.nt) {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
+                for (int i = 0; i < 8; ++i) {
                     if (j0 + i >= nin) break;
                     st4(Yo + __ldg(ty + j0 + i) + d.yoff[t0], acc[i][0] * scale,
                         acc[i][1] * scale, acc[i][2] * scale, acc[i][3] * scale);
@@ -374,7 +386,7 @@ __global__ void __launch_bounds__(256, 3) k_absorb_dense(const __grid_constant__
             }
         } else {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            for (int i = 0; i < 8; ++i) {
                 if (j0 + i >= nin) break;
                 const int oy = __ldg(ty + j0 + i);
 #pragma unroll

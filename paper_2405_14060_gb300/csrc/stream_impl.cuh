@@ -510,7 +510,7 @@ static void absorb_dense_go(const ADesc &d, int ym, cudaStream_t st) {
     const int64_t ntile = d.nouter * ((d.nin + AD_P - 1) / AD_P);
     const int64_t cap = std::max<int64_t>(1, (152LL * bps) / std::max(1, d.nbeta));
     dim3 grid((unsigned)std::max<int64_t>(1, std::min(ntile, cap)), (unsigned)d.nbeta, 1);
-    k_absorb_dense<T, XM><<<grid, 256, smem, st>>>(d, ym);
+    k_absorb_dense<T, XM><<<grid, AD_T, smem, st>>>(d, ym);
 }
 
 // Does the absorb run as k_absorb_dense (more than 256 combinations after
