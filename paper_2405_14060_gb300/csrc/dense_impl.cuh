@@ -13,9 +13,9 @@
 //                    positions x 4 new combinations and reads 16-byte vectors
 //                    of both (three shared loads per 32 multiply-adds).
 //   k_reduce_dense   O[g, s, t] = sum_m X[g, m, s] Z[g, m, t]: tiles of 64
-//                    positions of both operands staged as [s | t][p]; eight
-//                    thread groups take an eighth of each tile's positions,
-//                    each thread 8 x 4 outputs of the 32 x 32 block; per-block
+//                    positions of both operands staged as [p][s | t]; four
+//                    thread groups take a quarter of each tile's positions,
+//                    each thread 4 x 4 outputs of the 32 x 32 block; per-block
 //                    partials summed by the group's last block in a fixed order
 //                    (deterministic).
 #pragma once
@@ -408,7 +408,7 @@ constexpr int RD_S = 3;     // tile buffers
 
 // Per tile buffer: the [64 rows: X s, then Z t][RD_P + pad] tile and, for
 // each operand copied as planned chunks (chunk mode), a staging area of its
-// 32 x RD_P entries in memory order.  The final per-group sums [8][1024]
+// 32 x RD_P entries in memory order.  The final per-group sums [4][1024]
 // reuse the buffers.
 template <typename T>
 __host__ __device__ constexpr int rd_tile() {
@@ -516,12 +516,12 @@ __global__ void __launch_bounds__(256) k_reduce_dense(const __grid_constant__ RD
         }
         cp_async_commit();
     };
-    // thread: positions [8 pq, 8 pq + 8) of each tile, outputs
-    // s = ts + 4 i (i < 8), t = tt + 8 j (j < 4)
-    const int pq = tid >> 5, ts = (tid >> 3) & 3, tt = tid & 7;
-    T acc[8][4];
+    // thread: positions [16 pq, 16 pq + 16) of each tile, outputs
+    // s = ts + 8 i, t = tt + 8 j (i, j < 4)
+    const int pq = tid >> 6, ts = (tid >> 3) & 7, tt = tid & 7;
+    T acc[4][4];
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
     issue(0, 0);
@@ -551,17 +551,17 @@ __global__ void __launch_bounds__(256) k_reduce_dense(const __grid_constant__ RD
             __syncthreads();
         }
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int p = 8 * pq + 4 * q;
-            T xv[8][4], zv[4][4];
+        for (int q = 0; q < 4; ++q) {
+            const int p = 16 * pq + 4 * q;
+            T xv[4][4], zv[4][4];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) ld4(tb + (ts + 4 * i) * RR + p, xv[i]);
+            for (int i = 0; i < 4; ++i) ld4(tb + (ts + 8 * i) * RR + p, xv[i]);
 #pragma unroll
             for (int j = 0; j < 4; ++j) ld4(tb + (32 + tt + 8 * j) * RR + p, zv[j]);
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int i = 0; i < 8; ++i)
+                for (int i = 0; i < 4; ++i)
 #pragma unroll
                     for (int j = 0; j < 4; ++j) acc[i][j] += xv[i][u] * zv[j][u];
         }
@@ -569,20 +569,17 @@ __global__ void __launch_bounds__(256) k_reduce_dense(const __grid_constant__ RD
     }
     cp_async_wait<0>();
     __syncthreads();
-    // the eight position groups' sums (fixed order), then this block's
-    // partial row
-    T *red = Ts;   // [8][1024]
+    // the four position groups' sums, then this block's partial row
+    T *red = Ts;   // [4][1024]
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) red[pq * 1024 + (ts + 4 * i) * 32 + tt + 8 * j] = acc[i][j];
+        for (int j = 0; j < 4; ++j) red[pq * 1024 + (ts + 8 * i) * 32 + tt + 8 * j] = acc[i][j];
     __syncthreads();
     const T scale = sx * sz;
     T *prow = part + (g * nchunks + blockIdx.x) * 1024;
     for (int o = tid; o < 1024; o += 256)
-        prow[o] = (((red[o] + red[1024 + o]) + (red[2048 + o] + red[3072 + o])) +
-                   ((red[4096 + o] + red[5120 + o]) + (red[6144 + o] + red[7168 + o]))) *
-                  scale;
+        prow[o] = ((red[o] + red[1024 + o]) + (red[2048 + o] + red[3072 + o])) * scale;
     __threadfence();
     __syncthreads();
     __shared__ bool last;
