@@ -60,11 +60,21 @@ def _dense_model(layout, seed):
     dense absorb (24 x 20 combinations, more than the register-blocked
     kernels take), its adjoint A-bar another (20 x 24) and W'-bar a dense
     reduce.  layout "sfast": A's summed labels fastest (four at a time);
-    "mixed": A's labels interleaved (one entry at a time)."""
+    "mixed": A's labels interleaved (planned 16-byte chunks); "ternary":
+    ternary position labels and 30 x 30 combinations (one entry at a
+    time)."""
     rng = np.random.default_rng(seed)
-    r, s, t = list(range(12)), [12, 13, 14, 15], [16, 17, 18]
-    card = np.array([2] * 12 + [3, 2, 2, 2] + [5, 2, 2], np.int32)
-    sa = r + s if layout == "sfast" else [s[0]] + r[:6] + [s[1], s[2]] + r[6:] + [s[3]]
+    if layout == "ternary":
+        # 8 ternary positions (no 16-byte quads, no repeating 128-position
+        # tiles) and 30 x 30 combinations: the one-entry-per-copy and
+        # one-entry-per-store modes
+        r, s, t = list(range(8)), [8, 9, 10], [11, 12, 13]
+        card = np.array([3] * 8 + [3, 5, 2] + [5, 3, 2], np.int32)
+        sa = r + s
+    else:
+        r, s, t = list(range(12)), [12, 13, 14, 15], [16, 17, 18]
+        card = np.array([2] * 12 + [3, 2, 2, 2] + [5, 2, 2], np.int32)
+        sa = r + s if layout == "sfast" else [s[0]] + r[:6] + [s[1], s[2]] + r[6:] + [s[3]]
     scopes = [np.array(sa, np.int32), np.array(s + t, np.int32), np.array(t + r, np.int32)]
     tables = [rng.uniform(0.5, 1.5, size=int(np.prod(card[sc]))) for sc in scopes]
     m = synth.Model(card, scopes, tables, "MARKOV", "dense_" + layout)
@@ -84,7 +94,7 @@ def _dense_model(layout, seed):
     return m, left, right
 
 
-@pytest.mark.parametrize("layout", ["sfast", "mixed"])
+@pytest.mark.parametrize("layout", ["sfast", "mixed", "ternary"])
 def test_dense_absorb_and_reduce_nodes(layout):
     m, left, right = _dense_model(layout, 7)
     M = tn.Model.from_synth(m)
